@@ -1,0 +1,607 @@
+"""Pins of the CPU oracle to things other than itself (no GPU).
+
+Each test checks the oracle against a closed form, an invariant, a textbook
+table, or a convergence order fixed by the mathematics of the scheme of
+Mocz et al. (2013), Sec. 2, so that a dropped term, a wrong sign or index, or a
+transposed operand anywhere in the oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1305_5536_gb300 import ics
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------
+# Quadrature and mass matrices (Sec. 2.2: M = int (x^2, xy; xy, y^2) over the cell;
+# 2D magnetic block int (y^2, 0, xy; 0, x^2, -xy; xy, -xy, x^2+y^2))
+# ----------------------------------------------------------------------------
+
+def test_mass_matrices_closed_form():
+    P = O.Problem(O.MHD, 2, (5, 7), box=(1.0, 2.1))
+    dx, dy = P.h[0], P.h[1]
+    V = dx * dy
+    MT, MB = P.mass_matrices()
+    np.testing.assert_allclose(MT, V * np.diag([1.0, dx * dx / 12, dy * dy / 12]), rtol=1e-14,
+                               atol=1e-14 * V)
+    np.testing.assert_allclose(
+        MB, V * np.diag([1.0, 1.0, dy * dy / 12, dx * dx / 12, (dx * dx + dy * dy) / 12]),
+        rtol=1e-14, atol=1e-14 * V)
+    P3 = O.Problem(O.EULER, 3, (3, 4, 5), box=(1.0, 1.3, 0.7))
+    MT3, _ = P3.mass_matrices()
+    h = P3.h
+    V3 = h[0] * h[1] * h[2]
+    np.testing.assert_allclose(
+        MT3, V3 * np.diag([1.0, h[0] ** 2 / 12, h[1] ** 2 / 12, h[2] ** 2 / 12]), rtol=1e-14,
+        atol=1e-14 * V3)
+
+
+# ----------------------------------------------------------------------------
+# Physical flux (Sec. 2.1, eq. `cons`): the eigenvalues of dF/dU are the
+# characteristic speeds of the Euler and ideal-MHD systems.
+# ----------------------------------------------------------------------------
+
+def _prim_to_cons(W, g):
+    rho, vx, vy, vz, p, bx, by, bz = W
+    return np.array([rho, rho * vx, rho * vy, rho * vz,
+                     p / (g - 1) + 0.5 * rho * (vx * vx + vy * vy + vz * vz) +
+                     0.5 * (bx * bx + by * by + bz * bz), bx, by, bz])
+
+
+def _jac(U, d, g, idx):
+    J = np.zeros((len(idx), len(idx)))
+    for a, j in enumerate(idx):
+        h = 1e-6 * max(1.0, abs(U[j]))
+        Up, Um = U.copy(), U.copy()
+        Up[j] += h
+        Um[j] -= h
+        J[:, a] = (O.phys_flux(Up, d, g)[idx] - O.phys_flux(Um, d, g)[idx]) / (2 * h)
+    return J
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_euler_flux_eigenvalues(d):
+    g = 1.4
+    W = np.array([1.3, 0.4, -0.7, 0.25, 2.2, 0, 0, 0])
+    U = _prim_to_cons(W, g)
+    ev = np.sort(np.linalg.eigvals(_jac(U, d, g, [0, 1, 2, 3, 4])).real)
+    u, c = W[1 + d], math.sqrt(g * W[4] / W[0])
+    np.testing.assert_allclose(ev, [u - c, u, u, u, u + c], atol=2e-6)
+
+
+@pytest.mark.parametrize("d", [0, 1])
+def test_mhd_flux_eigenvalues(d):
+    g = 5.0 / 3.0
+    W = np.array([1.1, 0.3, -0.2, 0.1, 0.9, 0.8, -0.5, 0.4])
+    U = _prim_to_cons(W, g)
+    idx = [i for i in range(8) if i != 5 + d]  # the normal field is not a wave variable
+    ev = np.sort(np.linalg.eigvals(_jac(U, d, g, idx)).real)
+    rho, p = W[0], W[4]
+    B2 = (W[5:] ** 2).sum()
+    bn2 = W[5 + d] ** 2
+    a2, b2 = g * p / rho, B2 / rho
+    cf = math.sqrt(0.5 * (a2 + b2 + math.sqrt((a2 + b2) ** 2 - 4 * a2 * bn2 / rho)))
+    cs = math.sqrt(0.5 * (a2 + b2 - math.sqrt((a2 + b2) ** 2 - 4 * a2 * bn2 / rho)))
+    ca = math.sqrt(bn2 / rho)
+    u = W[1 + d]
+    np.testing.assert_allclose(ev, sorted([u - cf, u - ca, u - cs, u, u + cs, u + ca, u + cf]),
+                               atol=2e-6)
+
+
+# ----------------------------------------------------------------------------
+# Exact Riemann solver (Sec. 2.3)
+# ----------------------------------------------------------------------------
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def _half_ulp_of_printed(s):
+    s = s.lstrip("-")
+    if "." in s:
+        return 0.5 * 10.0 ** (-(len(s.split(".")[1])))
+    return 0.5
+
+
+def test_exact_riemann_toro_table():
+    for row in _golden_rows("toro_exact_riemann_star.txt"):
+        vals = [float(v) for v in row]
+        W, star, flags = O.exact_sample(vals[0:3], vals[3:6], 1.4, [0.0])
+        assert flags == 0
+        for k, col in ((0, 6), (1, 7)):
+            # the inputs of test 5 are themselves rounded to 6 figures: allow 1e-5
+            tol = max(1.2 * _half_ulp_of_printed(row[col]), 1e-5 * abs(vals[col]))
+            assert abs(star[k] - vals[col]) <= tol, (row, star)
+
+
+def _cons_1d(W, g):
+    rho, u, p = W[..., 0], W[..., 1], W[..., 2]
+    E = p / (g - 1) + 0.5 * rho * u * u
+    return np.stack([rho, rho * u, E], -1), np.stack([rho * u, rho * u * u + p, u * (E + p)], -1)
+
+
+@pytest.mark.parametrize("case", [(1.0, 0.0, 1.0, 0.125, 0.0, 0.1),
+                                  (1.0, 0.0, 1.0, 0.25, 0.0, 0.1795),
+                                  (1.0, 0.0, 30.0, 0.125, 0.0, 0.14)])
+def test_exact_riemann_invariants(case):
+    """Rankine-Hugoniot across the shock, isentropy and the Riemann invariant in
+    the rarefaction, continuity of p and u across the contact."""
+    g = 1.4
+    WL, WR = np.array(case[:3]), np.array(case[3:])
+    xi = np.linspace(-5, 10, 150001)
+    W, star, flags = O.exact_sample(WL, WR, g, xi)
+    assert flags == 0
+    ps, us = star
+    U, F = _cons_1d(W, g)
+    # shock: the largest density jump right of the contact
+    right = xi > us + 1e-3
+    jumps = np.abs(np.diff(W[:, 0]))
+    jumps[~right[1:]] = 0
+    k = int(np.argmax(jumps))
+    dU, dF = U[k + 1] - U[k], F[k + 1] - F[k]
+    s = dF[0] / dU[0]
+    scale = np.abs(F[k]).max() + np.abs(F[k + 1]).max()
+    assert abs(dF[1] - s * dU[1]) < 1e-12 * scale
+    assert abs(dF[2] - s * dU[2]) < 1e-12 * scale
+    assert xi[k] <= s <= xi[k + 1]
+    # rarefaction fan (left): isentropic, left Riemann invariant constant, xi = u - c
+    cL = math.sqrt(g * WL[2] / WL[0])
+    cs = cL * (ps / WL[2]) ** ((g - 1) / (2 * g))
+    fan = (xi > WL[1] - cL + 1e-3) & (xi < us - cs - 1e-3)
+    assert fan.sum() > 100
+    Wf = W[fan]
+    np.testing.assert_allclose(Wf[:, 2] / Wf[:, 0] ** g, WL[2] / WL[0] ** g, rtol=1e-12)
+    c = np.sqrt(g * Wf[:, 2] / Wf[:, 0])
+    np.testing.assert_allclose(Wf[:, 1] + 2 * c / (g - 1), WL[1] + 2 * cL / (g - 1), rtol=1e-12)
+    np.testing.assert_allclose(Wf[:, 1] - c, xi[fan], atol=1e-12)
+    # contact: p and u continuous, rho jumps
+    a, b = np.searchsorted(xi, us) - 2, np.searchsorted(xi, us) + 2
+    np.testing.assert_allclose(W[a, 1:], W[b, 1:], rtol=1e-12)
+    assert abs(W[a, 0] - W[b, 0]) > 1e-3
+
+
+def test_exact_riemann_flux_consistency_and_upwinding():
+    g = 5.0 / 3.0
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        W = np.array([rng.uniform(0.5, 2), rng.uniform(-1, 1), rng.uniform(-1, 1),
+                      rng.uniform(-1, 1), rng.uniform(0.5, 2), 0, 0, 0])
+        U = _prim_to_cons(W, g)
+        for d in range(3):
+            F, f = O.riemann(O.EXACT, U, U, d, g)
+            assert f == 0
+            np.testing.assert_allclose(F, O.phys_flux(U, d, g), rtol=1e-13, atol=1e-14)
+    # supersonic to the right: the Godunov flux is the left physical flux
+    WL = np.array([1.0, 3.0, 0.2, 0.0, 1.0, 0, 0, 0])
+    WR = np.array([0.5, 2.5, -0.1, 0.0, 0.6, 0, 0, 0])
+    UL, UR = _prim_to_cons(WL, g), _prim_to_cons(WR, g)
+    F, f = O.riemann(O.EXACT, UL, UR, 0, g)
+    np.testing.assert_allclose(F, O.phys_flux(UL, 0, g), rtol=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# HLLD (Sec. 2.3)
+# ----------------------------------------------------------------------------
+
+def _hllc_reference(WL, WR, g):
+    """HLLC flux (Toro, ch. 10) with the outer speeds min/max(u) -+ max(c): the
+    solver HLLD reduces to when B = 0.  Written independently of the oracle."""
+    def parts(W):
+        rho, u, v, w, p = W[0], W[1], W[2], W[3], W[4]
+        E = p / (g - 1) + 0.5 * rho * (u * u + v * v + w * w)
+        U = np.array([rho, rho * u, rho * v, rho * w, E])
+        F = np.array([rho * u, rho * u * u + p, rho * u * v, rho * u * w, u * (E + p)])
+        return U, F, math.sqrt(g * p / rho), E
+    UL, FL, cL, EL = parts(WL)
+    UR, FR, cR, ER = parts(WR)
+    SL = min(WL[1], WR[1]) - max(cL, cR)
+    SR = max(WL[1], WR[1]) + max(cL, cR)
+    if SL > 0:
+        return FL
+    if SR < 0:
+        return FR
+    SM = (WR[4] - WL[4] + WL[0] * WL[1] * (SL - WL[1]) - WR[0] * WR[1] * (SR - WR[1])) / \
+         (WL[0] * (SL - WL[1]) - WR[0] * (SR - WR[1]))
+
+    def star(W, U, S, E):
+        rho, u = W[0], W[1]
+        f = rho * (S - u) / (S - SM)
+        return f * np.array([1.0, SM, W[2], W[3], E / rho + (SM - u) * (SM + W[4] / (rho * (S - u)))])
+    if SM >= 0:
+        return FL + SL * (star(WL, UL, SL, EL) - UL)
+    return FR + SR * (star(WR, UR, SR, ER) - UR)
+
+
+def test_hlld_reduces_to_hllc_without_field():
+    g = 5.0 / 3.0
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        WL = np.array([rng.uniform(0.3, 2), rng.uniform(-1.5, 1.5), rng.uniform(-1, 1),
+                       rng.uniform(-1, 1), rng.uniform(0.3, 2), 0, 0, 0])
+        WR = np.array([rng.uniform(0.3, 2), rng.uniform(-1.5, 1.5), rng.uniform(-1, 1),
+                       rng.uniform(-1, 1), rng.uniform(0.3, 2), 0, 0, 0])
+        F, f = O.riemann(O.HLLD, _prim_to_cons(WL, g), _prim_to_cons(WR, g), 0, g)
+        assert f == 0
+        ref = _hllc_reference(WL, WR, g)
+        np.testing.assert_allclose(F[:5], ref, rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(F[5:], 0.0, atol=1e-15)
+
+
+def test_hlld_consistency_contact_and_normal_flux():
+    g = 5.0 / 3.0
+    rng = np.random.default_rng(12)
+    for _ in range(30):
+        W = np.array([rng.uniform(0.3, 2), rng.uniform(-1, 1), rng.uniform(-1, 1), 0.0,
+                      rng.uniform(0.3, 2), rng.uniform(-1, 1), rng.uniform(-1, 1), 0.0])
+        U = _prim_to_cons(W, g)
+        for d in range(2):
+            F, f = O.riemann(O.HLLD, U, U, d, g)
+            assert f == 0
+            np.testing.assert_allclose(F, O.phys_flux(U, d, g), rtol=1e-12, atol=1e-13)
+            assert F[5 + d] == 0.0
+    # an isolated stationary contact (only rho jumps, Bn != 0) is resolved exactly
+    WL = np.array([1.0, 0.0, 0.3, 0.0, 1.0, 0.7, -0.4, 0.0])
+    WR = WL.copy()
+    WR[0] = 0.3
+    F, f = O.riemann(O.HLLD, _prim_to_cons(WL, g), _prim_to_cons(WR, g), 0, g)
+    np.testing.assert_allclose(F, O.phys_flux(_prim_to_cons(WL, g), 0, g), atol=1e-13)
+    # supersonic: upwind physical flux
+    WL = np.array([1.0, 4.0, 0.3, 0.0, 1.0, 0.5, 0.4, 0.0])
+    WR = np.array([0.5, 3.5, -0.3, 0.0, 0.5, 0.5, -0.2, 0.0])
+    UL = _prim_to_cons(WL, g)
+    F, f = O.riemann(O.HLLD, UL, _prim_to_cons(WR, g), 0, g)
+    np.testing.assert_allclose(F, O.phys_flux(UL, 0, g), rtol=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# Whole-step invariants: free stream, conservation (Sec. 2.2, eq. `fv`:
+# the cell-average update is conservative), divergence-free magnetic basis
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("eq,dim", [(O.EULER, 2), (O.EULER, 3), (O.MHD, 2)])
+def test_free_stream(eq, dim):
+    n = (6, 5, 4)[:dim]
+    P = O.Problem(eq, dim, n, box=(1.0, 0.8, 1.2)[:dim], limiter=1)
+    if dim == 2:
+        prim = (1.3, 0.7, -0.4, 2.0) + ((0.5, -0.8) if eq == O.MHD else ())
+        u = ics.project_2d(lambda X, Y: prim, n, box=(1.0, 0.8), eq=eq)
+    else:
+        u = np.zeros(P.shape)
+        rho, v, p = 1.3, (0.7, -0.4, 0.2), 2.0
+        for k, val in enumerate([rho, rho * v[0], rho * v[1], rho * v[2],
+                                 p / (5 / 3 - 1) + 0.5 * rho * sum(x * x for x in v)]):
+            u[k * 4] = val
+    dt, f = P.cfl_dt(u)
+    out, _, f = P.run(u, 3, dt=dt)
+    assert f == 0
+    np.testing.assert_allclose(out, u, atol=1e-13 * np.abs(u).max())
+
+
+@pytest.mark.parametrize("eq,dim,lim", [(O.EULER, 2, 1), (O.EULER, 3, 1), (O.MHD, 2, 1),
+                                        (O.MHD, 2, 0)])
+def test_conservation(eq, dim, lim):
+    if eq == O.MHD:
+        n = (24, 20)
+        u = ics.orszag_tang(n)
+    elif dim == 2:
+        n = (24, 20)
+        u = ics.euler2d_wave(n, noise=1e-2)
+    else:
+        n = (8, 8, 8)
+        u = ics.kh3d(n, w0=0.1)
+    P = O.Problem(eq, dim, n, limiter=lim)
+    t0 = P.totals(u)
+    out, dts, f = P.run(u, 4)
+    assert f == 0
+    t1 = P.totals(out)
+    scale = np.abs(t0).max()
+    np.testing.assert_allclose(t1, t0, atol=2e-14 * scale)
+
+
+def test_magnetic_basis_divergence_free():
+    """Every cell polynomial of B is exactly divergence free (Sec. 2.2)."""
+    n = (16, 16)
+    P = O.Problem(O.MHD, 2, n)
+    u = ics.orszag_tang(n)
+    rng = np.random.default_rng(3)
+    u = u + 0.05 * rng.standard_normal(u.shape)  # arbitrary coefficients
+    out, _ = P.step(ics.orszag_tang(n), 1e-3)
+    for arr in (u, out):
+        for cell in rng.integers(0, 256, 8):
+            x = rng.uniform(-0.02, 0.02, 3)
+            x[2] = 0
+            h = 1e-4
+            dBx = (P.eval(arr, cell, x + [h, 0, 0])[5] - P.eval(arr, cell, x - [h, 0, 0])[5]) / (2 * h)
+            dBy = (P.eval(arr, cell, x + [0, h, 0])[6] - P.eval(arr, cell, x - [0, h, 0])[6]) / (2 * h)
+            assert abs(dBx + dBy) < 1e-8 * (abs(dBx) + 1)
+
+
+def test_divb_stokes_estimate():
+    """Sec. 2.6: zero for a uniform field; for a smooth divergence-free field it
+    measures only the face jumps and falls at second order with resolution."""
+    P = O.Problem(O.MHD, 2, (8, 8))
+    u = ics.project_2d(lambda X, Y: (1.0, 0.0, 0.0, 1.0, 0.3, -0.2), (8, 8), eq=O.MHD)
+    assert np.abs(P.divb(u)).max() < 1e-14
+    # a generic divergence-free field (curl of a random stream function): the
+    # face jumps of its P1 projection vanish with resolution
+    errs = []
+    for N in (16, 32, 64):
+        u = ics.mhd_random_smooth(N, rng=np.random.default_rng(4))
+        errs.append(np.abs(O.Problem(O.MHD, 2, (N, N)).divb(u)).mean())
+    assert errs[0] / errs[1] > 1.8 and errs[1] / errs[2] > 1.8, errs
+    # a field with a true divergence: B = (x, 0) locally gives div B = 1
+    Bx = lambda X, Y: 0.05 * np.sin(2 * np.pi * X)
+    N = 64
+    u = ics.project_2d(lambda X, Y: (1.0, 0.0, 0.0, 1.0, Bx(X, Y), 0.0 * X), (N, N), eq=O.MHD)
+    xc = (np.arange(N) + 0.5) / N
+    ref = 0.05 * 2 * np.pi * np.cos(2 * np.pi * xc)
+    np.testing.assert_allclose(O.Problem(O.MHD, 2, (N, N)).divb(u)[0], ref, atol=2e-3 * 0.32)
+
+
+# ----------------------------------------------------------------------------
+# Limiter (Sec. 2.5)
+# ----------------------------------------------------------------------------
+
+def _prim_grad_2d(u, g, mhd=False):
+    """Primitive centroid values and gradients from 2D coefficients (test-side)."""
+    rho, rx, ry = u[0], u[1], u[2]
+    mx, mxx, mxy = u[3], u[4], u[5]
+    my, myx, myy = u[6], u[7], u[8]
+    E, Ex, Ey = u[9], u[10], u[11]
+    vx, vy = mx / rho, my / rho
+    if mhd:
+        b1, b2, a1, a2, a3 = u[12], u[13], u[14], u[15], u[16]
+        B2 = b1 * b1 + b2 * b2
+        BgX = b1 * a3 + b2 * a2
+        BgY = b1 * a1 - b2 * a3
+    else:
+        B2 = BgX = BgY = 0.0
+    p = (g - 1) * (E - 0.5 * rho * (vx * vx + vy * vy) - 0.5 * B2)
+    out = {"rho": (rho, rx, ry)}
+    vxx, vxy = (mxx - vx * rx) / rho, (mxy - vx * ry) / rho
+    vyx, vyy = (myx - vy * rx) / rho, (myy - vy * ry) / rho
+    out["vx"] = (vx, vxx, vxy)
+    out["vy"] = (vy, vyx, vyy)
+    px = (g - 1) * (Ex - 0.5 * (vx * vx + vy * vy) * rx - rho * (vx * vxx + vy * vyx) - BgX)
+    py = (g - 1) * (Ey - 0.5 * (vx * vx + vy * vy) * ry - rho * (vx * vxy + vy * vyy) - BgY)
+    out["p"] = (p, px, py)
+    if mhd:
+        out["Bx"] = (b1, a3, a1)
+        out["By"] = (b2, a2, -a3)
+    return out
+
+
+@pytest.mark.parametrize("mhd", [False, True])
+def test_limiter_bounds_property(mhd):
+    """After limiting, the linear reconstruction of every primitive at every face
+    centroid lies within the min/max of the cell and its face neighbours."""
+    n = (12, 10)
+    g = 5.0 / 3.0
+    rng = np.random.default_rng(5)
+    if mhd:
+        u = ics.orszag_tang(n)
+    else:
+        u = ics.euler2d_wave(n, noise=0.0)
+    u = u.copy()
+    nT = 4
+    for v in range(nT):
+        for k in (1, 2):
+            u[v * 3 + k] += rng.uniform(-2, 2, u.shape[1:]) * np.abs(u[v * 3]).mean() * 3
+    if mhd:
+        u[14:17] += rng.uniform(-1, 1, (3,) + u.shape[1:])
+    P = O.Problem(O.MHD if mhd else O.EULER, 2, n, limiter=1)
+    ul, f = P.limit(u)
+    assert f == 0
+    np.testing.assert_array_equal(ul[0::3][:4], u[0::3][:4])  # averages untouched
+    dx, dy = P.h[0], P.h[1]
+    prims = _prim_grad_2d(ul, g, mhd)
+    for name, (phi, gx, gy) in prims.items():
+        nb = [np.roll(phi, s, a) for a in (0, 1) for s in (1, -1)]
+        hi = np.maximum.reduce([phi] + nb)
+        lo = np.minimum.reduce([phi] + nb)
+        tol = 1e-9 * (np.abs(phi).max() + 1)
+        for face in (phi + gx * dx / 2, phi - gx * dx / 2, phi + gy * dy / 2, phi - gy * dy / 2):
+            assert (face <= hi + tol).all() and (face >= lo - tol).all(), name
+    # the limiter only shrinks slopes: alpha in [0, 1]
+    pr0 = _prim_grad_2d(u, g, mhd)
+    for name in prims:
+        for a in (1, 2):
+            s0, s1 = pr0[name][a], prims[name][a]
+            ratio = np.where(np.abs(s0) > 1e-12, s1 / np.where(s0 == 0, 1, s0), 1.0)
+            assert (ratio >= -1e-9).all() and (ratio <= 1 + 1e-9).all(), name
+
+
+def test_limiter_keeps_linear_data_and_shared_field_factor():
+    n = (16, 16)
+    P = O.Problem(O.EULER, 2, n, limiter=1)
+    # density linear in x on the interior; v and p uniform
+    u = ics.project_2d(lambda X, Y: (2.0 + X, 0.3, -0.2, 1.5), n)
+    ul, _ = P.limit(u)
+    interior = (slice(None), slice(None), slice(1, -1))
+    np.testing.assert_allclose(ul[interior], u[interior], rtol=1e-12, atol=1e-14)
+    # MHD: one factor for (a1, a2, a3)
+    PM = O.Problem(O.MHD, 2, n, limiter=1)
+    um = ics.orszag_tang(n).copy()
+    rng = np.random.default_rng(9)
+    um[14:17] = um[14:17] * rng.uniform(1, 4, (3,) + um.shape[1:]) + \
+        rng.choice([-1.0, 1.0], (3,) + um.shape[1:]) * rng.uniform(0.5, 2.0, (3,) + um.shape[1:])
+    ulm, _ = PM.limit(um)
+    r = ulm[14:17] / um[14:17]
+    np.testing.assert_allclose(r[0], r[1], rtol=1e-12)
+    np.testing.assert_allclose(r[0], r[2], rtol=1e-12)
+    assert (r <= 1 + 1e-12).all() and r.min() < 0.99
+
+
+# ----------------------------------------------------------------------------
+# Convergence orders fixed by the mathematics of the P1 scheme
+# ----------------------------------------------------------------------------
+
+def _order(errs):
+    return [math.log(errs[i] / errs[i + 1], 2) for i in range(len(errs) - 1)]
+
+
+def test_convergence_advected_density_wave_2d():
+    """Smooth density wave translated by v = (1, 1): the exact solution is the
+    shifted initial field; second order in L1 (limiter off)."""
+    errs = []
+    T = 0.125
+    for N in (16, 32, 64):
+        u0 = ics.euler2d_wave((N, N), noise=0.0)
+        P = O.Problem(O.EULER, 2, (N, N), limiter=0)
+        dt0, _ = P.cfl_dt(u0, 0.3)
+        ns = int(math.ceil(T / dt0))
+        out, _, f = P.run(u0, ns, dt=T / ns)
+        assert f == 0
+        ex = ics.project_2d(lambda X, Y: (1 + 0.2 * np.sin(2 * np.pi * (X + Y - 2 * T)), 1.0, 1.0,
+                                          1.0), (N, N))
+        errs.append(np.abs(out[0] - ex[0]).mean())
+    o = _order(errs)
+    assert o[-1] > 1.85, (errs, o)
+
+
+def test_convergence_acoustic_wave():
+    """Sec. 3.1: acoustic wave, drho/rho = 1e-6, rho = 1, p = 3/5, gamma = 5/3
+    (sound speed 1), one period; second order in L1 (limiter off)."""
+    errs = []
+    for N in (16, 32, 64):
+        A = 1e-6
+
+        def f(X, Y):
+            s = A * np.sin(2 * np.pi * X)
+            return 1 + s, s, 0.0, 0.6 + s
+
+        u0 = ics.project_2d(f, (N, 1), box=(1.0, 1.0 / N))
+        P = O.Problem(O.EULER, 2, (N, 1), box=(1.0, 1.0 / N), limiter=0)
+        dt0, _ = P.cfl_dt(u0, 0.3)
+        ns = int(math.ceil(1.0 / dt0))
+        out, _, fl = P.run(u0, ns, dt=1.0 / ns)
+        errs.append(np.abs(out[0] - u0[0]).mean())
+    o = _order(errs)
+    assert o[-1] > 1.85, (errs, o)
+
+
+def _sod_exact_averages(N, t, L=20.0):
+    g = 1.4
+    WL, WR = (1.0, 0.0, 1.0), (0.25, 0.0, 0.1795)
+    dx = L / N
+    xs = -L + (np.arange(2 * N) + 0.5) * dx
+    sub = (np.arange(64) + 0.5) / 64 - 0.5
+    pts = (xs[:, None] + dx * sub[None, :]).ravel()
+    W, _, _ = O.exact_sample(WL, WR, g, pts / t)
+    return xs, W[:, 0].reshape(2 * N, 64).mean(1)
+
+
+def test_sod_first_order_convergence():
+    """Sec. 3.2: Sod tube variant (rho, p) = (1, 1) | (0.25, 0.1795), gamma = 1.4, t = 5;
+    the limited scheme converges to the exact solution at first order in L1."""
+    g, T, L = 1.4, 5.0, 20.0
+    errs = []
+    for N in (64, 128, 256):
+        # periodic box [-20, 20): left state on [-20, 0), right state on [0, 20)
+        nx = 2 * N
+
+        def f(X, Y):
+            x = X - L
+            left = x < 0
+            return np.where(left, 1.0, 0.25), 0.0, 0.0, np.where(left, 1.0, 0.1795)
+
+        u0 = ics.project_2d(f, (nx, 1), box=(2 * L, L / N), gamma=g)
+        P = O.Problem(O.EULER, 2, (nx, 1), box=(2 * L, L / N), gamma=g, limiter=1)
+        t, u = 0.0, u0
+        while t < T - 1e-12:
+            dt, _ = P.cfl_dt(u, 0.3)
+            dt = min(dt, T - t)
+            u, fl = P.step(u, dt)
+            assert fl == 0
+            t += dt
+        xs, ex = _sod_exact_averages(N, T, L)
+        win = np.abs(xs) < 10
+        errs.append(np.abs(u[0, 0][win] - ex[win]).mean())
+    # first order overall (Sec. 3.2); the pairwise ratio oscillates with the
+    # position of the shock inside its cell
+    overall = math.log(errs[0] / errs[-1], 2) / (len(errs) - 1)
+    assert errs[0] > errs[1] > errs[2] and 0.7 < overall < 1.3, (errs, overall)
+
+
+def test_convergence_mhd_advected_density_with_field():
+    """MHD contact wave: rho = 1 + 0.2 sin 2 pi (x + y), uniform v, p and B is an
+    exact solution (a translated density); second order (limiter off)."""
+    errs = []
+    T = 0.05
+    for N in (16, 32):
+        f = lambda X, Y: (1 + 0.2 * np.sin(2 * np.pi * (X + Y)), 1.0, 1.0, 1.0, 0.3, -0.2)
+        u0 = ics.project_2d(f, (N, N), eq=O.MHD)
+        P = O.Problem(O.MHD, 2, (N, N), limiter=0)
+        dt0, _ = P.cfl_dt(u0, 0.3)
+        ns = int(math.ceil(T / dt0))
+        out, _, fl = P.run(u0, ns, dt=T / ns)
+        assert fl == 0
+        ex = ics.project_2d(lambda X, Y: (1 + 0.2 * np.sin(2 * np.pi * (X + Y - 2 * T)), 1.0, 1.0,
+                                          1.0, 0.3, -0.2), (N, N), eq=O.MHD)
+        errs.append(np.abs(out[0] - ex[0]).mean())
+        np.testing.assert_allclose(out[12:14], ex[12:14], atol=1e-13)
+    assert _order(errs)[-1] > 1.8, errs
+
+
+def test_convergence_mhd_alfven_wave():
+    """Linear Alfven wave along k = 2 pi (1, 1) with B0 = (1, 1)/sqrt 2 parallel to k:
+    dB = eps sin(phase) (-1, 1)/sqrt 2, dv = -dB (rho = 1), speed |B0| = 1; the
+    magnetic field evolves through the divergence-free basis; second order."""
+    eps, T = 1e-3, 0.08
+    s2 = math.sqrt(2.0)
+    errs = []
+
+    def field(X, Y, t):
+        s = eps * np.sin(2 * np.pi * (X + Y - s2 * t))
+        bx, by = 1 / s2 - s / s2, 1 / s2 + s / s2
+        return 1.0, s / s2, -s / s2, 1.0, bx, by
+
+    for N in (16, 32):
+        u0 = ics.project_2d(lambda X, Y: field(X, Y, 0.0), (N, N), eq=O.MHD)
+        P = O.Problem(O.MHD, 2, (N, N), limiter=0)
+        dt0, _ = P.cfl_dt(u0, 0.3)
+        ns = int(math.ceil(T / dt0))
+        out, _, fl = P.run(u0, ns, dt=T / ns)
+        assert fl == 0
+        ex = ics.project_2d(lambda X, Y: field(X, Y, T), (N, N), eq=O.MHD)
+        errs.append(np.abs(out[13] - ex[13]).mean() + np.abs(out[12] - ex[12]).mean())
+    assert _order(errs)[-1] > 1.8, errs
+
+
+# ----------------------------------------------------------------------------
+# Tangent model used to check the GPU adjoint: against central differences
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lim", [0, 1])
+def test_tangent_matches_central_differences(lim):
+    n = (6, 5)
+    # every primitive varies between cells, so that no cell sits on a tie of the
+    # limiter's min/max (a kink where central differences are meaningless)
+    # (phases chosen so that no two neighbours tie by symmetry either)
+    f = lambda X, Y: (1 + 0.2 * np.sin(2 * np.pi * (X + Y) + 0.31),
+                      0.5 + 0.1 * np.sin(2 * np.pi * X + 0.47),
+                      -0.3 + 0.1 * np.cos(2 * np.pi * Y + 0.23),
+                      1 + 0.1 * np.sin(2 * np.pi * (X - 2 * Y) + 0.11))
+    u = ics.add_slope_noise(ics.project_2d(f, n), O.EULER, 2, 0.3, np.random.default_rng(1))
+    P = O.Problem(O.EULER, 2, n, limiter=lim)
+    rng = np.random.default_rng(2)
+    du = rng.standard_normal(u.shape) * 1e-2
+    dt = 0.5 * P.cfl_dt(u)[0]
+    out, dout, f = P.tangent_step(u, du, dt)
+    ref, _ = P.step(u, dt)
+    np.testing.assert_allclose(out, ref, rtol=1e-14, atol=1e-15)
+    eps = 1e-6
+    up, _ = P.step(u + eps * du, dt)
+    um, _ = P.step(u - eps * du, dt)
+    fd = (up - um) / (2 * eps)
+    np.testing.assert_allclose(dout, fd, atol=1e-7 * np.abs(fd).max())
