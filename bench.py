@@ -1,0 +1,357 @@
+"""Throughput of the GB300 DG step: cell-updates/s and HBM-roofline fraction.
+
+Default workload: 2D ideal MHD Orszag-Tang vortex, 512 x 512 cells, P1 DG with the
+locally divergence-free magnetic basis, min/max limiter, HLLD fluxes, CFL 0.3;
+FP32 arithmetic with FP64 cell averages (``value``), the FP64 path measured on
+the same workload beside it.  One "step" is one SSP-RK2 step of the whole grid.
+
+Timing: W warm-up steps, then K steps timed one by one with CUDA events on the
+solver's stream; the L2 cache is flushed (a 512 MiB buffer is written) before
+every timed step because the 512^2 state fits in L2.  Kernel durations come from
+CUDA events the library records around each stage-kernel launch.  Multi-GPU
+(--gpus N under torchrun): independent replicas, one per rank (weak scaling),
+barrier + max over ranks.  ``--impl reference`` times the CPU oracle instead.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 512 << 20
+
+WORKLOADS = {
+    "orszag_tang_512": dict(eq="mhd", dim=2, n=(512, 512), desc=(
+        "2D ideal MHD Orszag-Tang vortex 512x512, P1 DG, div-free B basis, HLLD, "
+        "min/max limiter, CFL 0.3")),
+    "smooth_wave_64": dict(eq="euler", dim=2, n=(64, 64), desc=(
+        "2D Euler smooth density wave 64x64 + 1e-3 slope noise, exact Riemann, "
+        "limiter, CFL 0.3")),
+    "kh3d_256": dict(eq="euler", dim=3, n=(256, 256, 256), desc=(
+        "3D Euler Kelvin-Helmholtz shear layer 256^3, exact Riemann, limiter, CFL 0.3")),
+}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def _src_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1305_5536_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.startswith("dg_stage") or f == "dg_physics.cuh" or f == "dg_common.cuh":
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, workload):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("src_sha") != _src_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+        self.window = (0.0, float("inf"))
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        t0, t1 = self.window
+        for ts, ln in self.lines:
+            if not (t0 <= ts <= t1 + 0.06):
+                continue
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as tdist
+
+    from paper_1305_5536_gb300 import dg, ics
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        tdist.init_process_group("nccl")
+    W = WORKLOADS[args.workload]
+    if W["eq"] == "mhd":
+        u0 = ics.orszag_tang(W["n"])
+    elif W["dim"] == 3:
+        u0 = ics.kh3d(W["n"])
+    else:
+        u0 = ics.euler2d_wave(W["n"])
+    ncell = int(np.prod(W["n"]))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    def measure(prec, K, Wm, with_clock):
+        s = dg.DGSolver(W["eq"], W["dim"], W["n"], precision=prec, cfl=0.3)
+        s.set_state(u0)
+        for _ in range(Wm):
+            flush.fill_(1.0)
+            s.step(1)
+        s.sync()
+        s.profile(True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(K)]
+        barrier()
+        sampler = ClockSampler(local) if with_clock else None
+        if sampler:
+            sampler.__enter__()
+            time.sleep(1.0)  # let nvidia-smi start sampling before the timed region
+        t_wall = time.perf_counter()
+        t_start = t_wall
+        for k in range(K):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            s.step(1)
+            evs[k][1].record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+        if sampler:
+            sampler.window = (t_start, t_start + t_wall)
+            time.sleep(0.2)
+            sampler.__exit__()
+        s.sync()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        kms, kn = s.profile_read()
+        s.profile(False)
+        tot = sum(step_ms)
+        if ws > 1:
+            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            tot = float(t.item())
+        res = dict(ms_total=tot, ms_per_step=tot / K, kernel_ms=kms, kernel_launches=kn,
+                   bytes=[s.stage_bytes(1), s.stage_bytes(2)], wall_s=t_wall,
+                   clocks=sampler.summary() if sampler else None)
+        # end to end through the public API with host buffers (pinned)
+        host_in = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        e2e_K = max(3, min(K, 20))
+        s.set_state(host_in)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(e2e_K):
+            s.set_state(host_in)
+            s.step(1)
+            s.get_state(host_out)
+        e1.record(stream)
+        barrier()
+        res["e2e_ms_per_step"] = e0.elapsed_time(e1) / e2e_K
+        res["e2e_bytes"] = host_in.numel() * 8
+        s.close()
+        return res
+
+    r32 = measure("fp32", args.steps, args.warmup, True)
+    r64 = measure("fp64", max(3, min(args.steps, 20)), max(3, args.warmup), False)
+    if rank != 0:
+        return
+    hbm, peak_kind = _peaks()
+    value = ws * ncell / (r32["ms_per_step"] * 1e-3)
+    # dominant kernel by time: stage 2 (reads two states, writes one)
+    k = 1 if r32["kernel_ms"][1] >= r32["kernel_ms"][0] else 0
+    avg_ms = r32["kernel_ms"][k] / max(r32["kernel_launches"][k], 1)
+    achieved = r32["bytes"][k] / (avg_ms * 1e-3) / 1e9
+    kname = "stage2d_kernel<%s,float,float,stage%d>" % (W["eq"], k + 1)
+    traffic = _traffic(kname, args.workload)
+    v64 = ws * ncell / (r64["ms_per_step"] * 1e-3)
+    out = {
+        "metric": "DG cell-updates/sec (SSP-RK2 steps x cells / s)",
+        "value": value,
+        "unit": "cell-updates/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": r32["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (analytic initial condition projected onto the P1 bases)",
+        "config": {"workload": W["desc"], "grid": list(W["n"]),
+                   "precision": "FP32 arithmetic + FP32 derivative coefficients, FP64 averages",
+                   "l2": "flushed (512 MiB write) before every timed step",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic,
+                     "algorithmic_bytes_per_launch": r32["bytes"][k],
+                     "avg_launch_ms": avg_ms},
+        "kernels": {"stage1_ms_avg": r32["kernel_ms"][0] / max(r32["kernel_launches"][0], 1),
+                    "stage2_ms_avg": r32["kernel_ms"][1] / max(r32["kernel_launches"][1], 1),
+                    "launches": r32["kernel_launches"]},
+        "fp64": {"value": v64, "ms_per_step": r64["ms_per_step"],
+                 "speedup_fp32_over_fp64": v64 and value / v64,
+                 "stage_ms_avg": [r64["kernel_ms"][i] / max(r64["kernel_launches"][i], 1)
+                                  for i in range(2)]},
+        "e2e": {"value": ws * ncell / (r32["e2e_ms_per_step"] * 1e-3), "unit": "cell-updates/s",
+                "h2d_bytes_per_step": r32["e2e_bytes"], "d2h_bytes_per_step": r32["e2e_bytes"]},
+        "gpu_launches": int(sum(r32["kernel_launches"])),
+        "clocks": r32["clocks"],
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload, u0)
+    print(json.dumps(out))
+
+
+def _oracle_problem(workload):
+    import oracle as O
+    W = WORKLOADS[workload]
+    return O.Problem(O.MHD if W["eq"] == "mhd" else O.EULER, W["dim"], W["n"])
+
+
+def cpu_baseline(workload, u0, budget_s=12.0, max_steps=50):
+    """The CPU oracle, as it stands, on one host core: whole-grid SSP-RK2 steps
+    of the same workload until ~budget_s of CPU time."""
+    P = _oracle_problem(workload)
+    dt = P.cfl_dt(u0)[0]
+    u = u0
+    n = 0
+    t0 = time.perf_counter()
+    while n < max_steps:
+        u, _ = P.step(u, dt)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    ncell = int(np.prod(WORKLOADS[workload]["n"]))
+    return {"value": n * ncell / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "%d whole-grid SSP-RK2 steps of the same workload (%.1f s)" % (n, el)}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    from paper_1305_5536_gb300 import ics
+    W = WORKLOADS[args.workload]
+    if W["eq"] == "mhd":
+        u0 = ics.orszag_tang(W["n"])
+    elif W["dim"] == 3:
+        u0 = ics.kh3d(W["n"])
+    else:
+        u0 = ics.euler2d_wave(W["n"])
+    P = _oracle_problem(args.workload)
+    ncell = int(np.prod(W["n"]))
+    dt = P.cfl_dt(u0)[0]
+    u = u0
+    for _ in range(args.warmup):
+        u, _ = P.step(u, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u, _ = P.step(u, dt)
+    el = time.perf_counter() - t0
+    v = args.steps * ncell / el
+    print(json.dumps({
+        "impl": "reference", "metric": "DG cell-updates/sec (SSP-RK2 steps x cells / s)",
+        "value": v, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": W["desc"], "grid": list(W["n"])},
+        "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d whole-grid steps" % args.steps},
+        "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="orszag_tang_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,66 @@
+// dg_common.cuh -- shared device/host definitions of the DG kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dgk {
+
+// Per-problem control block in device memory.  The Courant time step of the
+// current state is cfl / vmax_cur; stage 2 of a step accumulates the signal speed
+// of the new state into vmax_next (bit pattern of a positive double, so that the
+// integer atomicMax orders it), and the last CTA to finish moves it to vmax_cur.
+struct Ctl {
+  double vmax_cur;
+  unsigned long long vmax_next;
+  double t;
+  double dt_last;
+  long long step;
+  unsigned int ticket;
+  unsigned int err;
+  double* dt_hist;      // optional record of the time steps (adjoint)
+  long long hist_cap;
+};
+
+// One state: FP64 cell averages [nv][ncell] and derivative coefficients
+// [ns][ncell] of type TS (double or float).
+template <class TS>
+struct StateBuf {
+  double* c0;
+  TS* sl;
+};
+
+// Arguments of one stage launch on one periodic 2D grid.
+template <class TS>
+struct Stage2DArgs {
+  int nx, ny;
+  long ncell;
+  double dx, dy;
+  double gamma, cfl, dt_override;
+  int limiter;
+  StateBuf<TS> in;    // stage input (V^n in stage 1, V^1 in stage 2)
+  StateBuf<TS> base;  // V^n (stage 2 only)
+  StateBuf<TS> out;
+  Ctl* ctl;
+};
+
+// Arguments of one stage launch on one periodic 3D grid.
+template <class TS>
+struct Stage3DArgs {
+  int nx, ny, nz;
+  long ncell;
+  double dx, dy, dz;
+  double gamma, cfl, dt_override;
+  int limiter;
+  StateBuf<TS> in;
+  StateBuf<TS> base;
+  StateBuf<TS> out;
+  Ctl* ctl;
+};
+
+__host__ __device__ __forceinline__ int wrap_index(int g, int n) {
+  int r = g % n;
+  return r < 0 ? r + n : r;
+}
+
+}  // namespace dgk

@@ -1,0 +1,339 @@
+// dg_physics.cuh -- device physics of the P1 DG step (sm_103a).
+//
+// Inline device functions, templated on the arithmetic type T (double for the
+// FP64 path, float for the FP32 path):
+//   * gas constants and the fast magnetosonic speed (Sec. 2.1),
+//   * the exact Riemann solver of the Euler equations (Sec. 2.3; Newton iteration
+//     on the pressure function with the adaptive PVRS/TRRS/TSRS first guess of
+//     Toro's textbook, sampled at x/t = 0),
+//   * the HLLD solver of Miyoshi & Kusano (2005) for planar ideal MHD (Sec. 2.3),
+//   * the min/max slope limiter of one cell on primitive variables (Sec. 2.5).
+// Face solvers work in the face frame: normal velocity u, transverse velocities,
+// and return fluxes in that frame.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace dgk {
+
+enum : unsigned {
+  ERR_NONPHYS = 1u,   // rho <= 0 or p <= 0 at an evaluated state
+  ERR_VACUUM = 2u,    // the exact solver met a vacuum-generating pair
+  ERR_NEWTON = 4u,    // Newton iteration for p* did not converge
+};
+
+template <class T> struct Prec;
+template <> struct Prec<double> {
+  static constexpr double newton_tol = 1e-12;
+  static constexpr int newton_max = 50;
+  static constexpr double hlld_degenerate = 1e-8;
+};
+template <> struct Prec<float> {
+  static constexpr float newton_tol = 1e-5f;
+  static constexpr int newton_max = 20;
+  static constexpr float hlld_degenerate = 1e-8f;
+};
+
+__device__ __forceinline__ double rpow(double x, double e) { return pow(x, e); }
+__device__ __forceinline__ float rpow(float x, float e) { return powf(x, e); }
+__device__ __forceinline__ double rsqrtv(double x) { return sqrt(x); }
+__device__ __forceinline__ float rsqrtv(float x) { return sqrtf(x); }
+
+// Constants of the equation of state p_gas = (gamma - 1) rho u.
+template <class T>
+struct Gas {
+  T g, gm1, gp1, inv_gm1;
+  T z;        // (g-1)/(2g)
+  T inv_z;    // 2g/(g-1)
+  T mzp;      // -(g+1)/(2g)
+  T g6;       // (g-1)/(g+1)
+  T shk1;     // (g+1)/(2g)
+  T inv_g;    // 1/g
+  T two_gm1;  // 2/(g-1)
+  T two_gp1;  // 2/(g+1)
+  __host__ __device__ void set(double gamma) {
+    g = T(gamma);
+    gm1 = T(gamma - 1.0);
+    gp1 = T(gamma + 1.0);
+    inv_gm1 = T(1.0 / (gamma - 1.0));
+    z = T((gamma - 1.0) / (2.0 * gamma));
+    inv_z = T(2.0 * gamma / (gamma - 1.0));
+    mzp = T(-(gamma + 1.0) / (2.0 * gamma));
+    g6 = T((gamma - 1.0) / (gamma + 1.0));
+    shk1 = T((gamma + 1.0) / (2.0 * gamma));
+    inv_g = T(1.0 / gamma);
+    two_gm1 = T(2.0 / (gamma - 1.0));
+    two_gp1 = T(2.0 / (gamma + 1.0));
+  }
+};
+
+// Fast magnetosonic speed along a direction with normal field bn.
+template <class T>
+__device__ __forceinline__ T fast_speed(const Gas<T>& G, T rho, T p, T b2, T bn) {
+  T a2 = G.g * p / rho;
+  T bb = b2 / rho;
+  T bn2 = bn * bn / rho;
+  T s = a2 + bb;
+  T disc = s * s - T(4) * a2 * bn2;
+  disc = disc < T(0) ? T(0) : disc;
+  return rsqrtv(T(0.5) * (s + rsqrtv(disc)));
+}
+
+// ----------------------------------------------------------------------------
+// Exact Riemann solver (Euler).  NT transverse velocity components.
+// Output F[0] mass, F[1] normal momentum, F[2..1+NT] transverse momenta,
+// F[2+NT] energy -- all in the face frame.
+// ----------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void pressure_fn(const Gas<T>& G, T p, T rK, T pK, T cK, T& f,
+                                            T& df) {
+  if (p > pK) {
+    T A = G.two_gp1 / rK;
+    T B = G.g6 * pK;
+    T q = rsqrtv(A / (p + B));
+    f = (p - pK) * q;
+    df = q * (T(1) - T(0.5) * (p - pK) / (B + p));
+  } else {
+    T pr = p / pK;
+    f = T(2) * cK * G.inv_gm1 * (rpow(pr, G.z) - T(1));
+    df = T(1) / (rK * cK) * rpow(pr, G.mzp);
+  }
+}
+
+template <class T, int NT>
+__device__ __forceinline__ void exact_flux(const Gas<T>& G, T rL, T uL, T pL, const T* vtL, T rR,
+                                           T uR, T pR, const T* vtR, T* F, unsigned& err) {
+  if (!(rL > T(0) && pL > T(0) && rR > T(0) && pR > T(0))) {
+    err |= ERR_NONPHYS;
+    for (int q = 0; q < 3 + NT; ++q) F[q] = T(0);
+    return;
+  }
+  const T cL = rsqrtv(G.g * pL / rL), cR = rsqrtv(G.g * pR / rR);
+  const T du = uR - uL;
+  if (G.two_gm1 * (cL + cR) <= du) err |= ERR_VACUUM;
+  // first guess: PVRS inside its range, else two-rarefaction or two-shock
+  T pv = T(0.5) * (pL + pR) - T(0.125) * du * (rL + rR) * (cL + cR);
+  pv = pv > T(0) ? pv : T(0);
+  const T pmin = pL < pR ? pL : pR, pmax = pL < pR ? pR : pL;
+  T p;
+  if (pmax / pmin <= T(2) && pmin <= pv && pv <= pmax) {
+    p = pv;
+  } else if (pv < pmin) {
+    T num = cL + cR - T(0.5) * G.gm1 * du;
+    T den = cL / rpow(pL, G.z) + cR / rpow(pR, G.z);
+    p = rpow((num > T(0) ? num : T(0)) / den, G.inv_z);
+  } else {
+    T gL = rsqrtv(G.two_gp1 / rL / (G.g6 * pL + pv));
+    T gR = rsqrtv(G.two_gp1 / rR / (G.g6 * pR + pv));
+    p = (gL * pL + gR * pR - du) / (gL + gR);
+  }
+  const T pfloor = T(1e-10) * pmin;
+  if (!(p > pfloor)) p = pfloor;
+  bool conv = false;
+  for (int it = 0; it < Prec<T>::newton_max; ++it) {
+    T fL, dfL, fR, dfR;
+    pressure_fn(G, p, rL, pL, cL, fL, dfL);
+    pressure_fn(G, p, rR, pR, cR, fR, dfR);
+    T pn = p - (fL + fR + du) / (dfL + dfR);
+    if (!(pn > pfloor)) pn = pfloor;
+    T change = T(2) * fabs(pn - p) / (pn + p);
+    p = pn;
+    if (change < Prec<T>::newton_tol) { conv = true; break; }
+  }
+  if (!conv) err |= ERR_NEWTON;
+  T fL, dfL, fR, dfR;
+  pressure_fn(G, p, rL, pL, cL, fL, dfL);
+  pressure_fn(G, p, rR, pR, cR, fR, dfR);
+  const T us = T(0.5) * (uL + uR) + T(0.5) * (fR - fL);
+  // sample the self-similar solution at x/t = 0
+  T rho, u, pp;
+  const T* vt;
+  if (T(0) <= us) {
+    vt = vtL;
+    if (p > pL) {
+      T SL = uL - cL * rsqrtv(G.shk1 * p / pL + G.z);
+      if (T(0) <= SL) { rho = rL; u = uL; pp = pL; }
+      else { rho = rL * ((p / pL + G.g6) / (G.g6 * p / pL + T(1))); u = us; pp = p; }
+    } else {
+      T SHL = uL - cL;
+      if (T(0) <= SHL) { rho = rL; u = uL; pp = pL; }
+      else {
+        T cmL = cL * rpow(p / pL, G.z);
+        if (T(0) > us - cmL) { rho = rL * rpow(p / pL, G.inv_g); u = us; pp = p; }
+        else {
+          T c = G.two_gp1 * (cL + T(0.5) * G.gm1 * uL);
+          u = c;
+          rho = rL * rpow(c / cL, G.two_gm1);
+          pp = pL * rpow(c / cL, G.inv_z);
+        }
+      }
+    }
+  } else {
+    vt = vtR;
+    if (p > pR) {
+      T SR = uR + cR * rsqrtv(G.shk1 * p / pR + G.z);
+      if (T(0) >= SR) { rho = rR; u = uR; pp = pR; }
+      else { rho = rR * ((p / pR + G.g6) / (G.g6 * p / pR + T(1))); u = us; pp = p; }
+    } else {
+      T SHR = uR + cR;
+      if (T(0) >= SHR) { rho = rR; u = uR; pp = pR; }
+      else {
+        T cmR = cR * rpow(p / pR, G.z);
+        if (T(0) < us + cmR) { rho = rR * rpow(p / pR, G.inv_g); u = us; pp = p; }
+        else {
+          T c = G.two_gp1 * (cR - T(0.5) * G.gm1 * uR);
+          u = -c;
+          rho = rR * rpow(c / cR, G.two_gm1);
+          pp = pR * rpow(c / cR, G.inv_z);
+        }
+      }
+    }
+  }
+  T kin = u * u;
+#pragma unroll
+  for (int a = 0; a < NT; ++a) kin += vt[a] * vt[a];
+  const T E = pp * G.inv_gm1 + T(0.5) * rho * kin;
+  const T mu = rho * u;
+  F[0] = mu;
+  F[1] = mu * u + pp;
+#pragma unroll
+  for (int a = 0; a < NT; ++a) F[2 + a] = mu * vt[a];
+  F[2 + NT] = u * (E + pp);
+}
+
+// ----------------------------------------------------------------------------
+// HLLD solver, planar MHD (one transverse velocity v and field bt; out-of-plane
+// components are zero).  bn is the common normal field.  Output in the face
+// frame: F[0] mass, F[1] normal momentum, F[2] transverse momentum, F[3] energy,
+// F[4] flux of the transverse field (the normal-field flux is zero).
+// ----------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void hlld_flux(const Gas<T>& G, T rL, T uL, T vL, T pL, T btL, T rR,
+                                          T uR, T vR, T pR, T btR, T bn, T* F, unsigned& err) {
+  if (!(rL > T(0) && pL > T(0) && rR > T(0) && pR > T(0))) {
+    err |= ERR_NONPHYS;
+    for (int q = 0; q < 5; ++q) F[q] = T(0);
+    return;
+  }
+  const T bn2 = bn * bn;
+  const T b2L = bn2 + btL * btL, b2R = bn2 + btR * btR;
+  const T EL = pL * G.inv_gm1 + T(0.5) * rL * (uL * uL + vL * vL) + T(0.5) * b2L;
+  const T ER = pR * G.inv_gm1 + T(0.5) * rR * (uR * uR + vR * vR) + T(0.5) * b2R;
+  const T pTL = pL + T(0.5) * b2L, pTR = pR + T(0.5) * b2R;
+  const T cfL = fast_speed(G, rL, pL, b2L, bn), cfR = fast_speed(G, rR, pR, b2R, bn);
+  const T cmax = cfL > cfR ? cfL : cfR;
+  const T SL = (uL < uR ? uL : uR) - cmax;
+  const T SR = (uL < uR ? uR : uL) + cmax;
+  // physical fluxes and conserved vectors of both sides
+  T FL[5], FR[5], UL[5], UR[5];
+  {
+    T vB = uL * bn + vL * btL;
+    FL[0] = rL * uL; FL[1] = rL * uL * uL + pTL - bn2; FL[2] = rL * uL * vL - bn * btL;
+    FL[3] = (EL + pTL) * uL - bn * vB; FL[4] = btL * uL - vL * bn;
+    UL[0] = rL; UL[1] = rL * uL; UL[2] = rL * vL; UL[3] = EL; UL[4] = btL;
+    vB = uR * bn + vR * btR;
+    FR[0] = rR * uR; FR[1] = rR * uR * uR + pTR - bn2; FR[2] = rR * uR * vR - bn * btR;
+    FR[3] = (ER + pTR) * uR - bn * vB; FR[4] = btR * uR - vR * bn;
+    UR[0] = rR; UR[1] = rR * uR; UR[2] = rR * vR; UR[3] = ER; UR[4] = btR;
+  }
+  if (SL > T(0)) {
+    for (int q = 0; q < 5; ++q) F[q] = FL[q];
+    return;
+  }
+  if (SR < T(0)) {
+    for (int q = 0; q < 5; ++q) F[q] = FR[q];
+    return;
+  }
+  const T dL = SL - uL, dR = SR - uR;
+  const T den = dR * rR - dL * rL;
+  const T SM = (dR * rR * uR - dL * rL * uL - pTR + pTL) / den;
+  const T pTs = (dR * rR * pTL - dL * rL * pTR + rL * rR * dR * dL * (uR - uL)) / den;
+  // single-star states
+  T rsL, vsL, btsL, EsL, rsR, vsR, btsR, EsR;
+  {
+    T dd = rL * dL * (SL - SM) - bn2;
+    rsL = rL * dL / (SL - SM);
+    if (fabs(dd) < Prec<T>::hlld_degenerate * (rL * dL * dL + bn2)) {
+      vsL = vL; btsL = btL;
+    } else {
+      T tv = bn * (SM - uL) / dd;
+      T tb = (rL * dL * dL - bn2) / dd;
+      vsL = vL - btL * tv;
+      btsL = btL * tb;
+    }
+    T vB = uL * bn + vL * btL, vBs = SM * bn + vsL * btsL;
+    EsL = (dL * EL - pTL * uL + pTs * SM + bn * (vB - vBs)) / (SL - SM);
+    dd = rR * dR * (SR - SM) - bn2;
+    rsR = rR * dR / (SR - SM);
+    if (fabs(dd) < Prec<T>::hlld_degenerate * (rR * dR * dR + bn2)) {
+      vsR = vR; btsR = btR;
+    } else {
+      T tv = bn * (SM - uR) / dd;
+      T tb = (rR * dR * dR - bn2) / dd;
+      vsR = vR - btR * tv;
+      btsR = btR * tb;
+    }
+    vB = uR * bn + vR * btR;
+    vBs = SM * bn + vsR * btsR;
+    EsR = (dR * ER - pTR * uR + pTs * SM + bn * (vB - vBs)) / (SR - SM);
+  }
+  T UsL[5] = {rsL, rsL * SM, rsL * vsL, EsL, btsL};
+  T UsR[5] = {rsR, rsR * SM, rsR * vsR, EsR, btsR};
+  const T sqL = rsqrtv(rsL), sqR = rsqrtv(rsR);
+  const T SsL = SM - fabs(bn) / sqL, SsR = SM + fabs(bn) / sqR;
+  if (SsL >= T(0)) {
+    for (int q = 0; q < 5; ++q) F[q] = FL[q] + SL * (UsL[q] - UL[q]);
+    return;
+  }
+  if (SsR <= T(0)) {
+    for (int q = 0; q < 5; ++q) F[q] = FR[q] + SR * (UsR[q] - UR[q]);
+    return;
+  }
+  // double-star states between the Alfven waves
+  const T sg = bn > T(0) ? T(1) : (bn < T(0) ? T(-1) : T(0));
+  const T inv = T(1) / (sqL + sqR);
+  const T vss = (sqL * vsL + sqR * vsR + (btsR - btsL) * sg) * inv;
+  const T btss = (sqL * btsR + sqR * btsL + sqL * sqR * (vsR - vsL) * sg) * inv;
+  const T vBss = SM * bn + vss * btss;
+  if (SM >= T(0)) {
+    T vBsL = SM * bn + vsL * btsL;
+    T E2 = EsL - sqL * (vBsL - vBss) * sg;
+    T U2[5] = {rsL, rsL * SM, rsL * vss, E2, btss};
+    for (int q = 0; q < 5; ++q)
+      F[q] = FL[q] + SL * (UsL[q] - UL[q]) + SsL * (U2[q] - UsL[q]);
+  } else {
+    T vBsR = SM * bn + vsR * btsR;
+    T E2 = EsR + sqR * (vBsR - vBss) * sg;
+    T U2[5] = {rsR, rsR * SM, rsR * vss, E2, btss};
+    for (int q = 0; q < 5; ++q)
+      F[q] = FR[q] + SR * (UsR[q] - UR[q]) + SsR * (U2[q] - UsR[q]);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Min/max limiter coefficient of one primitive (Sec. 2.5):
+//   alpha = min(1, min_faces psi_f), psi_f = (phimax - phi)/dphi_f (dphi_f > 0),
+//   (phimin - phi)/dphi_f (dphi_f < 0), 1 (dphi_f = 0), dphi_f = grad phi . (f - s).
+// On a Cartesian cell the faces along axis d have dphi = +-a_d with
+// a_d = g_d h_d / 2, so min_faces psi = min(phimax - phi, phi - phimin) / max_d |a_d|
+// (division is monotone, so this is the same floating-point value).
+// ----------------------------------------------------------------------------
+template <class T, int DIM>
+__device__ __forceinline__ T limiter_alpha(T phi, T phimax, T phimin, const T* grad,
+                                           const T* half_h) {
+  T amax = T(0);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    T a = fabs(grad[d] * half_h[d]);
+    amax = a > amax ? a : amax;
+  }
+  if (!(amax > T(0))) return T(1);
+  T up = phimax - phi, dn = phi - phimin;
+  T m = up < dn ? up : dn;
+  T psi = m / amax;
+  return psi < T(1) ? psi : T(1);
+}
+
+}  // namespace dgk

@@ -1,0 +1,255 @@
+"""Python binding of the C ABI in ``include/dg.h`` (ctypes; argument marshalling only).
+
+Every step of the method runs in the CUDA kernels of ``libdg.so``; this module
+only converts arguments.  If the library is missing it raises -- there is no
+CPU fallback.  PyTorch is used for device memory and streams: torch CUDA tensors
+are passed to the library by their data pointers, numpy arrays as host memory.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libdg.so")
+
+DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONPHYS, DG_ETIMEOUT, DG_ESTATE = range(7)
+DG_EULER, DG_MHD = 0, 1
+DG_FP64, DG_FP32 = 0, 1
+DG_EXACT, DG_HLLD = 0, 1
+_STATUS = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_ENONPHYS",
+           5: "DG_ETIMEOUT", 6: "DG_ESTATE"}
+
+# every entry point declared in include/dg.h
+SYMBOLS = ["dg_num_planes", "dg_init", "dg_init_batch", "dg_destroy", "dg_last_error",
+           "dg_set_state", "dg_get_state", "dg_step", "dg_sync", "dg_get_times", "dg_totals",
+           "dg_divb", "dg_adjoint_step", "dg_record", "dg_adjoint", "dg_profile",
+           "dg_profile_read", "dg_stage_bytes"]
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class dg_config(ctypes.Structure):
+    _fields_ = [("eq", ctypes.c_int), ("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("box", ctypes.c_double * 3), ("gamma", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("limiter", ctypes.c_int),
+                ("precision", ctypes.c_int), ("riemann", ctypes.c_int),
+                ("ckpt_every", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load():
+    """Load libdg.so (building it first if it is missing and nvcc is present)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        from . import _build
+        _build.build()
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libdg.so is missing: the CUDA extension must be built "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(LIB_PATH)
+    P, c_int, c_double = ctypes.POINTER, ctypes.c_int, ctypes.c_double
+    vp = ctypes.c_void_p
+    pcfg = P(dg_config)
+    L.dg_num_planes.argtypes = [pcfg]
+    L.dg_init.argtypes = [pcfg, vp, P(vp)]
+    L.dg_init_batch.argtypes = [pcfg, c_int, vp, P(vp)]
+    L.dg_destroy.argtypes = [vp]
+    L.dg_destroy.restype = None
+    L.dg_last_error.argtypes = [vp]
+    L.dg_last_error.restype = ctypes.c_char_p
+    L.dg_set_state.argtypes = [vp, vp, c_int]
+    L.dg_get_state.argtypes = [vp, vp, c_int]
+    L.dg_step.argtypes = [vp, c_int, c_double, P(c_double)]
+    L.dg_sync.argtypes = [vp]
+    L.dg_get_times.argtypes = [vp, vp, vp]
+    L.dg_totals.argtypes = [vp, vp]
+    L.dg_divb.argtypes = [vp, vp, c_int]
+    L.dg_adjoint_step.argtypes = [vp, vp, vp, vp, c_double]
+    L.dg_record.argtypes = [vp, c_int, c_double, P(c_double)]
+    L.dg_adjoint.argtypes = [vp, vp, vp]
+    L.dg_profile.argtypes = [vp, c_int]
+    L.dg_profile_read.argtypes = [vp, P(c_double), P(ctypes.c_longlong)]
+    L.dg_stage_bytes.argtypes = [vp, c_int]
+    L.dg_stage_bytes.restype = c_double
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor (contiguous float64)."""
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+        return a.ctypes.data_as(ctypes.c_void_p), 0
+    import torch
+    assert isinstance(a, torch.Tensor) and a.dtype == torch.float64 and a.is_contiguous()
+    return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def make_config(eq="euler", dim=2, n=(64, 64), box=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, cfl=0.3,
+                limiter=1, precision="fp64", ckpt_every=0):
+    c = dg_config()
+    c.eq = DG_MHD if eq in ("mhd", DG_MHD) else DG_EULER
+    c.dim = dim
+    nn = list(n) + [1] * (3 - len(n))
+    bb = list(box) + [1.0] * (3 - len(box))
+    for a in range(3):
+        c.n[a] = int(nn[a])
+        c.box[a] = float(bb[a])
+    c.gamma, c.cfl, c.limiter = float(gamma), float(cfl), int(limiter)
+    c.precision = DG_FP32 if precision in ("fp32", DG_FP32) else DG_FP64
+    c.riemann = DG_HLLD if c.eq == DG_MHD else DG_EXACT
+    c.ckpt_every = int(ckpt_every)
+    return c
+
+
+class DGSolver:
+    """One periodic problem (or a batch of problems) stepped by the GPU library."""
+
+    def __init__(self, eq="euler", dim=2, n=(64, 64), box=(1.0, 1.0, 1.0), gamma=5.0 / 3.0,
+                 cfl=0.3, limiter=1, precision="fp64", ckpt_every=0, stream=None, configs=None):
+        L = load()
+        self._L = L
+        h = ctypes.c_void_p()
+        st = _current_stream() if stream is None else ctypes.c_void_p(stream)
+        if configs is None:
+            cfg = make_config(eq, dim, n, box, gamma, cfl, limiter, precision, ckpt_every)
+            self.configs = [cfg]
+            s = L.dg_init(ctypes.byref(cfg), st, ctypes.byref(h))
+        else:
+            arr = (dg_config * len(configs))(*configs)
+            self.configs = list(configs)
+            s = L.dg_init_batch(arr, len(configs), st, ctypes.byref(h))
+        if s != DG_OK:
+            raise DGError(s, L.dg_last_error(None).decode())
+        self._h = h
+        c0 = self.configs[0]
+        self.eq, self.dim = c0.eq, c0.dim
+        self.nplanes = L.dg_num_planes(ctypes.byref(c0))
+        self.shapes = []
+        for c in self.configs:
+            if c.dim == 2:
+                self.shapes.append((self.nplanes, c.n[1], c.n[0]))
+            else:
+                self.shapes.append((self.nplanes, c.n[2], c.n[1], c.n[0]))
+        self.size = sum(int(np.prod(s)) for s in self.shapes)
+
+    @property
+    def shape(self):
+        return self.shapes[0]
+
+    def _check(self, s):
+        if s != DG_OK:
+            raise DGError(s, self._L.dg_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.dg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, u):
+        p, dev = _ptr(u)
+        assert u.size == self.size if isinstance(u, np.ndarray) else u.numel() == self.size
+        self._check(self._L.dg_set_state(self._h, p, dev))
+
+    def get_state(self, out=None, device=None):
+        if out is None:
+            if device is not None:
+                import torch
+                out = torch.empty(self.size if len(self.shapes) > 1 else self.shape,
+                                  dtype=torch.float64, device=device)
+            else:
+                out = np.empty(self.size if len(self.shapes) > 1 else self.shape)
+        p, dev = _ptr(out)
+        self._check(self._L.dg_get_state(self._h, p, dev))
+        return out
+
+    def step(self, nsteps=1, dt=0.0, sync=False):
+        t = ctypes.c_double(0.0)
+        self._check(self._L.dg_step(self._h, int(nsteps), float(dt),
+                                    ctypes.byref(t) if sync else None))
+        return t.value if sync else None
+
+    def sync(self):
+        self._check(self._L.dg_sync(self._h))
+
+    def times(self):
+        n = len(self.configs)
+        t, dt = np.zeros(n), np.zeros(n)
+        self._check(self._L.dg_get_times(self._h, t.ctypes.data_as(ctypes.c_void_p),
+                                         dt.ctypes.data_as(ctypes.c_void_p)))
+        return t, dt
+
+    def totals(self):
+        nv = (4 if self.dim == 2 else 5) + (2 if self.eq == DG_MHD else 0)
+        out = np.zeros(nv * len(self.configs))
+        self._check(self._L.dg_totals(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out.reshape(len(self.configs), nv)
+
+    def divb(self):
+        c = self.configs[0]
+        out = np.zeros((c.n[1], c.n[0]))
+        self._check(self._L.dg_divb(self._h, out.ctypes.data_as(ctypes.c_void_p), 0))
+        return out
+
+    def adjoint_step(self, lam_next, u_n, dt, lam_prev=None):
+        import torch
+        if lam_prev is None:
+            lam_prev = torch.empty_like(lam_next)
+        self._check(self._L.dg_adjoint_step(self._h, ctypes.c_void_p(lam_next.data_ptr()),
+                                            ctypes.c_void_p(lam_prev.data_ptr()),
+                                            ctypes.c_void_p(u_n.data_ptr()), float(dt)))
+        return lam_prev
+
+    def record(self, nsteps, dt=0.0):
+        t = ctypes.c_double(0.0)
+        self._check(self._L.dg_record(self._h, int(nsteps), float(dt), ctypes.byref(t)))
+        return t.value
+
+    def adjoint(self, lam_N, lam_0=None):
+        import torch
+        if lam_0 is None:
+            lam_0 = torch.empty_like(lam_N)
+        self._check(self._L.dg_adjoint(self._h, ctypes.c_void_p(lam_N.data_ptr()),
+                                       ctypes.c_void_p(lam_0.data_ptr())))
+        return lam_0
+
+    def profile(self, enable=True):
+        self._check(self._L.dg_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        ms = (ctypes.c_double * 2)()
+        n = (ctypes.c_longlong * 2)()
+        self._check(self._L.dg_profile_read(self._h, ms, n))
+        return [ms[0], ms[1]], [n[0], n[1]]
+
+    def stage_bytes(self, stage):
+        return self._L.dg_stage_bytes(self._h, int(stage))
+
+
+def batch(configs, stream=None):
+    return DGSolver(configs=configs, stream=stream)

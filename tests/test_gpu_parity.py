@@ -1,0 +1,133 @@
+"""GPU (CUDA, sm_103a) path against the CPU oracle, through the C ABI.
+
+After one step with the same time step, the cell polynomials of every variable
+agree within 1e-12 (FP64) or 1e-5 (FP32 arithmetic and derivative coefficients,
+FP64 averages) relative to the variable's scale (tests/helpers.py).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1305_5536_gb300 import dg, ics
+
+from helpers import class_rel_err, poly_rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def _generic_euler(n, seed=3):
+    """Smooth state in which every primitive varies (no exact ties between
+    neighbours for the limiter), plus seeded slope noise."""
+    f = lambda X, Y: (1 + 0.2 * np.sin(2 * np.pi * (X + Y) + 0.31),
+                      0.5 + 0.2 * np.sin(2 * np.pi * X + 0.47),
+                      -0.3 + 0.2 * np.cos(2 * np.pi * Y + 0.23),
+                      1 + 0.1 * np.sin(2 * np.pi * (X - 2 * Y) + 0.11))
+    return ics.add_slope_noise(ics.project_2d(f, n), 0, 2, 0.05, np.random.default_rng(seed))
+
+
+def _one_step(eq, dim, n, u0, prec, limiter=1, box=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, frac=0.5):
+    P = O.Problem(O.MHD if eq == "mhd" else O.EULER, dim, n, box=box[:dim], gamma=gamma,
+                  limiter=limiter)
+    dt = frac * P.cfl_dt(u0)[0]
+    ref, fl = P.step(u0, dt)
+    assert fl == 0
+    s = dg.DGSolver(eq, dim, n, box=box, gamma=gamma, limiter=limiter, precision=prec)
+    s.set_state(u0)
+    s.step(1, dt=dt, sync=True)
+    got = s.get_state()
+    s.close()
+    return got, ref, P.h
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [(4, 4), (5, 3), (37, 29), (64, 64), (1, 7), (33, 1)])
+@pytest.mark.parametrize("limiter", [0, 1])
+def test_euler2d_one_step(prec, n, limiter):
+    u0 = _generic_euler(n)
+    got, ref, h = _one_step("euler", 2, n, u0, prec, limiter=limiter, box=(1.0, 0.9, 1.0))
+    err, where = poly_rel_err(got, ref, 0, 2, h)
+    assert err < TOL[prec], (err, where)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [(24, 20), (64, 64), (17, 5)])
+@pytest.mark.parametrize("limiter", [0, 1])
+def test_mhd2d_one_step(prec, n, limiter):
+    u0 = ics.orszag_tang(n)
+    got, ref, h = _one_step("mhd", 2, n, u0, prec, limiter=limiter)
+    err, where = poly_rel_err(got, ref, 1, 2, h)
+    assert err < TOL[prec], (err, where)
+
+
+def test_euler2d_smooth_wave_workload_fp64_50_steps():
+    """64x64 smooth density wave with slope noise, limiter on, 50 steps at CFL 0.3:
+    Courant time steps and final state match the oracle."""
+    n = (64, 64)
+    u0 = ics.euler2d_wave(n)
+    P = O.Problem(O.EULER, 2, n)
+    ref, dts, fl = P.run(u0, 50, cfl=0.3)
+    assert fl == 0
+    s = dg.DGSolver("euler", 2, n, precision="fp64", cfl=0.3)
+    s.set_state(u0)
+    t = s.step(50, sync=True)
+    got = s.get_state()
+    assert abs(t - dts.sum()) < 1e-13 * dts.sum()
+    err, where = poly_rel_err(got, ref, 0, 2, P.h)
+    assert err < 1e-11, (err, where)
+
+
+def test_orszag_tang_512_one_step_full_size():
+    """Full-size Orszag-Tang 512x512 (FP64 and FP32), one step, every cell."""
+    n = (512, 512)
+    u0 = ics.orszag_tang(n)
+    P = O.Problem(O.MHD, 2, n)
+    dt = P.cfl_dt(u0)[0]
+    ref, fl = P.step(u0, dt)
+    assert fl == 0
+    for prec in ("fp64", "fp32"):
+        s = dg.DGSolver("mhd", 2, n, precision=prec)
+        s.set_state(u0)
+        tnext = s.times()[1][0]
+        assert abs(tnext - dt) < (1e-14 if prec == "fp64" else 1e-6) * dt
+        s.step(1, dt=dt, sync=True)
+        err, where = poly_rel_err(s.get_state(), ref, 1, 2, P.h)
+        s.close()
+        assert err < TOL[prec], (prec, err, where)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_conservation_and_divb_on_gpu(prec):
+    n = (64, 64)
+    u0 = ics.orszag_tang(n)
+    s = dg.DGSolver("mhd", 2, n, precision=prec)
+    s.set_state(u0)
+    t0 = s.totals()[0]
+    s.step(20, sync=True)
+    t1 = s.totals()[0]
+    scale = np.abs(t0).max()
+    assert np.abs(t1 - t0).max() < (1e-13 if prec == "fp64" else 1e-6) * scale
+    P = O.Problem(O.MHD, 2, n)
+    np.testing.assert_allclose(s.divb(), P.divb(s.get_state()), atol=1e-12)
+
+
+def test_free_stream_gpu():
+    n = (16, 12)
+    u = ics.project_2d(lambda X, Y: (1.3, 0.7, -0.4, 2.0, 0.5, -0.8), n, eq=1)
+    s = dg.DGSolver("mhd", 2, n, precision="fp64")
+    s.set_state(u)
+    s.step(5, sync=True)
+    np.testing.assert_allclose(s.get_state(), u, atol=1e-13 * np.abs(u).max())
+
+
+def test_nonphysical_state_reports_status():
+    n = (8, 8)
+    u = ics.project_2d(lambda X, Y: (1.0, 0.0, 0.0, 1.0), n)
+    u[9] *= -1.0  # negative energy: negative pressure everywhere
+    s = dg.DGSolver("euler", 2, n)
+    with pytest.raises(dg.DGError) as ei:
+        s.set_state(u)
+    assert ei.value.status == dg.DG_ENONPHYS
