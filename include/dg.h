@@ -155,6 +155,27 @@ dg_status dg_record(dg_ctx* ctx, int nsteps, double dt_override, double* t_out);
  * (held fixed).  The context's current state is restored afterwards. */
 dg_status dg_adjoint(dg_ctx* ctx, const double* lam_N, double* lam_0);
 
+/* Conservation totals of a state held by the caller, for callers that may not
+ * allocate device memory (the paper has no counterpart: this is a service of the
+ * library, not a step of the method).  Same result as dg_totals -- V * sum of the
+ * cell averages of every conserved variable, FP64 with compensated summation,
+ * Taylor variables then (MHD) b1, b2 -- but without a context and without any
+ * cudaMalloc/cudaFree: the per-block partial sums live in one fixed 512 KiB
+ * static device array that every GPU loading the library keeps until exit.
+ *   cfg: grid and equations of the state (precision, limiter and cfl unused).
+ *   u: device pointer, interchange layout, float64.
+ *   out: nvar doubles, device (out_on_device != 0) or host memory; a host
+ *        result is waited for, a device one is only enqueued.
+ *   cuda_stream: stream for the work (NULL = legacy default stream).
+ * Limit: at most 16,777,216 cells (e.g. 256^3 or 4096^2); larger grids return
+ * DG_EINVAL.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race, so
+ * enqueue them one after another.  Failures are described by
+ * dg_last_error(NULL). */
+dg_status dg_totals_noalloc(const dg_config* cfg, const double* u, double* out,
+                            int out_on_device, void* cuda_stream);
+
 /* Kernel timing with CUDA events recorded on the context stream around every
  * stage-kernel launch (enable != 0), or stop (0).  Enabling clears the record
  * and disables CUDA-graph replay for the recorded steps. */

@@ -444,6 +444,8 @@ static dg_status get_state_t(dg_ctx* c, double* dst, int on_device) {
 
 }  // namespace
 
+void dgk::set_global_error(const std::string& msg) { g_err = msg; }
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

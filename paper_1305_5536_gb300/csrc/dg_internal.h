@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "dg_common.cuh"
 
 namespace dgk {
@@ -52,5 +54,8 @@ cudaError_t launch_totals(const double* c0, int nv, long ncell, double* partial,
 template <class TS>
 cudaError_t launch_divb(StateBuf<TS> s, int nx, int ny, double dx, double dy, double* out,
                         cudaStream_t st);
+
+// Message returned by dg_last_error(NULL) (failures without a context).
+void set_global_error(const std::string& msg);
 
 }  // namespace dgk

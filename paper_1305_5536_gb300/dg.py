@@ -24,7 +24,7 @@ _STATUS = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_ENO
 SYMBOLS = ["dg_num_planes", "dg_init", "dg_init_batch", "dg_destroy", "dg_last_error",
            "dg_set_state", "dg_get_state", "dg_step", "dg_sync", "dg_get_times", "dg_totals",
            "dg_divb", "dg_adjoint_step", "dg_record", "dg_adjoint", "dg_profile",
-           "dg_profile_read", "dg_stage_bytes"]
+           "dg_profile_read", "dg_stage_bytes", "dg_totals_noalloc"]
 
 
 class DGError(RuntimeError):
@@ -80,6 +80,7 @@ def load():
     L.dg_profile_read.argtypes = [vp, P(c_double), P(ctypes.c_longlong)]
     L.dg_stage_bytes.argtypes = [vp, c_int]
     L.dg_stage_bytes.restype = c_double
+    L.dg_totals_noalloc.argtypes = [pcfg, vp, vp, c_int, vp]
     _lib = L
     return L
 
@@ -249,6 +250,21 @@ class DGSolver:
 
     def stage_bytes(self, stage):
         return self._L.dg_stage_bytes(self._h, int(stage))
+
+
+def totals_noalloc(u, eq="euler", dim=2, n=(64, 64), box=(1.0, 1.0, 1.0), stream=None):
+    """Conservation totals of a caller-held device state (torch CUDA tensor,
+    interchange layout) without any device allocation by the library."""
+    L = load()
+    cfg = make_config(eq, dim, n, box)
+    nv = (4 if dim == 2 else 5) + (2 if cfg.eq == DG_MHD else 0)
+    out = np.zeros(nv)
+    st = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    s = L.dg_totals_noalloc(ctypes.byref(cfg), ctypes.c_void_p(u.data_ptr()),
+                            out.ctypes.data_as(ctypes.c_void_p), 0, st)
+    if s != DG_OK:
+        raise DGError(s, L.dg_last_error(None).decode())
+    return out
 
 
 def batch(configs, stream=None):
