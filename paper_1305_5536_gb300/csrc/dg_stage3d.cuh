@@ -1,0 +1,438 @@
+// dg_stage3d.cuh -- one SSP-RK2 stage of the 3D P1 DG scheme for the Euler
+// equations (Taylor basis 1, x, y, z; Sec. 2.2 eqs. `fv3d`, `dgderiv3d`) as one
+// fused kernel.
+//
+// One CTA owns a TX x TY x TZ tile.  Shared memory holds the centroid primitives
+// of the tile plus a halo of 2 cells (for the limiter's neighbour extrema), the
+// averages and derivative coefficients of the tile plus a halo of 1 cell, and one
+// face-flux buffer.  After the limiter (Sec. 2.5) has been applied in place to the
+// tile and its ring, the faces of each orientation are processed in turn: the
+// Riemann flux at the 2x2 Gauss points of every face of that orientation is
+// computed once into the buffer, then every cell adds its two faces to the
+// right-hand side it keeps in registers.
+//
+// With S = sum of a face's 4 Gauss-point fluxes and D_e = the difference between
+// the points on the + and - side of the transverse axis e, superscripts +/- the
+// faces at +/- dx_d/2, and sum_q over the 8 volume Gauss points:
+//   d avg/dt     += -(S+ - S-) / (4 dx_d)
+//   d U_d/dt     += 3/(2 dx_d^2) (sum_q F_d - (S+ + S-))
+//   d U_e/dt     += -sqrt3/(2 dx_e dx_d) (D_e+ - D_e-)       (e != d)
+#pragma once
+
+#include "dg_common.cuh"
+#include "dg_physics.cuh"
+
+namespace dgk {
+
+template <int TX, int TY, int TZ, class TC>
+__host__ __device__ constexpr int stage3d_face_max() {
+  return ((TX + 1) * TY * TZ > TX * (TY + 1) * TZ)
+             ? (((TX + 1) * TY * TZ > TX * TY * (TZ + 1)) ? (TX + 1) * TY * TZ
+                                                          : TX * TY * (TZ + 1))
+             : ((TX * (TY + 1) * TZ > TX * TY * (TZ + 1)) ? TX * (TY + 1) * TZ
+                                                          : TX * TY * (TZ + 1));
+}
+
+template <int TX, int TY, int TZ, class TC>
+__host__ __device__ constexpr size_t stage3d_smem_bytes() {
+  return (size_t(5) * (TX + 4) * (TY + 4) * (TZ + 4) + size_t(20) * (TX + 2) * (TY + 2) * (TZ + 2) +
+          size_t(5) * 4 * stage3d_face_max<TX, TY, TZ, TC>()) * sizeof(TC) +
+         sizeof(int) * ((TX + 4) + (TY + 4) + (TZ + 4));
+}
+
+template <class TC>
+__device__ __forceinline__ void prims3d(const Gas<TC>& G, const TC* c, TC* W, unsigned& err) {
+  TC rho = c[0], inv = TC(1) / rho;
+  TC vx = c[1] * inv, vy = c[2] * inv, vz = c[3] * inv;
+  TC p = G.gm1 * (c[4] - TC(0.5) * (c[1] * vx + c[2] * vy + c[3] * vz));
+  if (!(rho > TC(0) && p > TC(0))) err |= ERR_NONPHYS;
+  W[0] = rho; W[1] = vx; W[2] = vy; W[3] = vz; W[4] = p;
+}
+
+// Limit the 15 derivative coefficients s[v*3+d] of one cell; W its centroid
+// primitives, Wn[k] those of its 6 face neighbours.
+template <class TC>
+__device__ __forceinline__ void limit_cell3d(const Gas<TC>& G, const TC* hh, const TC* W,
+                                             const TC (*Wn)[5], TC* s) {
+  TC hi[5], lo[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    TC a = W[q], b = W[q];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      a = Wn[k][q] > a ? Wn[k][q] : a;
+      b = Wn[k][q] < b ? Wn[k][q] : b;
+    }
+    hi[q] = a;
+    lo[q] = b;
+  }
+  const TC rho = W[0], inv = TC(1) / rho;
+  const TC v[3] = {W[1], W[2], W[3]};
+  const TC v2h = TC(0.5) * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  TC gr[3], gv[3][3], gp[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    gr[d] = s[d];
+    TC vdv = TC(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      gv[i][d] = (s[3 * (1 + i) + d] - v[i] * gr[d]) * inv;
+      vdv += v[i] * gv[i][d];
+    }
+    gp[d] = G.gm1 * (s[12 + d] - v2h * gr[d] - rho * vdv);
+  }
+  const TC ar = limiter_alpha<TC, 3>(W[0], hi[0], lo[0], gr, hh);
+  TC av[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) av[i] = limiter_alpha<TC, 3>(W[1 + i], hi[1 + i], lo[1 + i], gv[i], hh);
+  const TC ap = limiter_alpha<TC, 3>(W[4], hi[4], lo[4], gp, hh);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    TC r = ar * gr[d];
+    TC vdv = TC(0);
+    s[d] = r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      TC u = av[i] * gv[i][d];
+      s[3 * (1 + i) + d] = rho * u + v[i] * r;
+      vdv += v[i] * u;
+    }
+    s[12 + d] = ap * gp[d] * G.inv_gm1 + v2h * r + rho * vdv;
+  }
+}
+
+template <class TC>
+__device__ __forceinline__ void eval3d(const TC* c0, const TC* s, TC x, TC y, TC z, TC* c) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) c[v] = c0[v] + s[3 * v] * x + s[3 * v + 1] * y + s[3 * v + 2] * z;
+}
+
+// Physical flux along axis d of conserved (rho, m, E).
+template <class TC>
+__device__ __forceinline__ void phys_flux3d(const Gas<TC>& G, const TC* c, int d, TC* F,
+                                            unsigned& err) {
+  TC rho = c[0], inv = TC(1) / rho;
+  TC v[3] = {c[1] * inv, c[2] * inv, c[3] * inv};
+  TC p = G.gm1 * (c[4] - TC(0.5) * (c[1] * v[0] + c[2] * v[1] + c[3] * v[2]));
+  if (!(rho > TC(0) && p > TC(0))) err |= ERR_NONPHYS;
+  TC vd = v[d];
+  F[0] = c[1 + d];
+  F[1] = c[1] * vd;
+  F[2] = c[2] * vd;
+  F[3] = c[3] * vd;
+  F[1 + d] += p;
+  F[4] = (c[4] + p) * vd;
+}
+
+// Exact-solver flux through a face along axis d between conserved cl, cr; lab
+// frame (rho, mx, my, mz, E).
+template <class TC>
+__device__ __forceinline__ void face_flux3d(const Gas<TC>& G, int d, const TC* cl, const TC* cr,
+                                            TC* F, unsigned& err) {
+  TC il = TC(1) / cl[0], ir = TC(1) / cr[0];
+  TC vl[3] = {cl[1] * il, cl[2] * il, cl[3] * il};
+  TC vr[3] = {cr[1] * ir, cr[2] * ir, cr[3] * ir};
+  TC pl = G.gm1 * (cl[4] - TC(0.5) * (cl[1] * vl[0] + cl[2] * vl[1] + cl[3] * vl[2]));
+  TC pr = G.gm1 * (cr[4] - TC(0.5) * (cr[1] * vr[0] + cr[2] * vr[1] + cr[3] * vr[2]));
+  const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  TC tl[2] = {vl[t1], vl[t2]}, tr[2] = {vr[t1], vr[t2]};
+  TC Ff[5];
+  exact_flux<TC, 2>(G, cl[0], vl[d], pl, tl, cr[0], vr[d], pr, tr, Ff, err);
+  F[0] = Ff[0];
+  F[1 + d] = Ff[1];
+  F[1 + t1] = Ff[2];
+  F[1 + t2] = Ff[3];
+  F[4] = Ff[4];
+}
+
+template <class TC, class TS, int TX, int TY, int TZ, int STAGE>
+__global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs<TS> A) {
+  constexpr int R2X = TX + 4, R2Y = TY + 4, R2Z = TZ + 4, R2 = R2X * R2Y * R2Z;
+  constexpr int R1X = TX + 2, R1Y = TY + 2, R1Z = TZ + 2, R1 = R1X * R1Y * R1Z;
+  constexpr int NT = TX * TY * TZ;
+  constexpr int FMAX = stage3d_face_max<TX, TY, TZ, TC>();
+  static_assert(NT % 32 == 0, "tile must be whole warps");
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* s_w = reinterpret_cast<TC*>(smem_raw);  // 5 x R2 primitives
+  TC* s_c0 = s_w + 5 * R2;                    // 5 x R1 averages
+  TC* s_sl = s_c0 + 5 * R1;                   // 15 x R1 derivatives
+  TC* s_f = s_sl + 15 * R1;                   // 5 x 4 x FMAX face fluxes
+  int* s_gx = reinterpret_cast<int*>(s_f + 5 * 4 * FMAX);
+  int* s_gy = s_gx + R2X;
+  int* s_gz = s_gy + R2Y;
+  __shared__ double s_dt;
+  __shared__ unsigned s_err;
+  __shared__ double s_red[NT / 32];
+
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * TZ;
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const size_t ncell = (size_t)A.ncell;
+  Gas<TC> G;
+  G.set(A.gamma);
+  unsigned err = 0;
+  if (tid == 0) {
+    s_err = 0;
+    double dt = A.dt_override > 0.0 ? A.dt_override : A.cfl / A.ctl->vmax_cur;
+    if (!(dt > 0.0) || !(dt < 1e300)) err |= ERR_NONPHYS;
+    s_dt = dt;
+  }
+  if (tid < R2X) s_gx[tid] = wrap_index(i0 - 2 + tid, nx);
+  else if (tid < R2X + R2Y) s_gy[tid - R2X] = wrap_index(j0 - 2 + (tid - R2X), ny) * nx;
+  else if (tid < R2X + R2Y + R2Z)
+    s_gz[tid - R2X - R2Y] = wrap_index(k0 - 2 + (tid - R2X - R2Y), nz) * nx * ny;
+  __syncthreads();
+
+  // ---- primitives of the halo-2 box; averages of the halo-1 box
+  for (int r = tid; r < R2; r += NT) {
+    int rz = r / (R2X * R2Y), rr = r - rz * (R2X * R2Y);
+    int ry = rr / R2X, rx = rr - ry * R2X;
+    size_t g = (size_t)s_gz[rz] + s_gy[ry] + s_gx[rx];
+    TC c[5], W[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) c[v] = (TC)__ldg(&A.in.c0[v * ncell + g]);
+    prims3d<TC>(G, c, W, err);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) s_w[q * R2 + r] = W[q];
+    if (rx >= 1 && rx <= TX + 2 && ry >= 1 && ry <= TY + 2 && rz >= 1 && rz <= TZ + 2) {
+      int r1 = ((rz - 1) * R1Y + (ry - 1)) * R1X + (rx - 1);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s_c0[v * R1 + r1] = c[v];
+    }
+  }
+  for (int e = tid; e < 15 * R1; e += NT) {
+    int v = e / R1, r = e - v * R1;
+    int rz = r / (R1X * R1Y), rr = r - rz * (R1X * R1Y);
+    int ry = rr / R1X, rx = rr - ry * R1X;
+    s_sl[e] = (TC)__ldg(&A.in.sl[v * ncell + (size_t)s_gz[rz + 1] + s_gy[ry + 1] + s_gx[rx + 1]]);
+  }
+  __syncthreads();
+
+  const TC dx = (TC)A.dx, dy = (TC)A.dy, dz = (TC)A.dz;
+  const TC hh[3] = {TC(0.5) * dx, TC(0.5) * dy, TC(0.5) * dz};
+  const TC oo[3] = {dx * TC(0.28867513459481288225), dy * TC(0.28867513459481288225),
+                    dz * TC(0.28867513459481288225)};
+
+  // ---- limiter on the tile and its ring
+  if (A.limiter) {
+    for (int r1 = tid; r1 < R1; r1 += NT) {
+      int rz = r1 / (R1X * R1Y), rr = r1 - rz * (R1X * R1Y);
+      int ry = rr / R1X, rx = rr - ry * R1X;
+      int r2 = ((rz + 1) * R2Y + (ry + 1)) * R2X + (rx + 1);
+      TC W[5], Wn[6][5], s[15];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        W[q] = s_w[q * R2 + r2];
+        Wn[0][q] = s_w[q * R2 + r2 - 1];
+        Wn[1][q] = s_w[q * R2 + r2 + 1];
+        Wn[2][q] = s_w[q * R2 + r2 - R2X];
+        Wn[3][q] = s_w[q * R2 + r2 + R2X];
+        Wn[4][q] = s_w[q * R2 + r2 - R2X * R2Y];
+        Wn[5][q] = s_w[q * R2 + r2 + R2X * R2Y];
+      }
+#pragma unroll
+      for (int k = 0; k < 15; ++k) s[k] = s_sl[k * R1 + r1];
+      limit_cell3d<TC>(G, hh, W, Wn, s);
+#pragma unroll
+      for (int k = 0; k < 15; ++k) s_sl[k * R1 + r1] = s[k];
+    }
+    __syncthreads();
+  }
+
+  // ---- per-cell state, volume integral
+  const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
+  const int r1c = ((lz + 1) * R1Y + (ly + 1)) * R1X + (lx + 1);
+  TC c0[5], s[15];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) c0[v] = s_c0[v * R1 + r1c];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) s[k] = s_sl[k * R1 + r1c];
+  TC rc0[5], rs[15];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) rc0[v] = TC(0);
+  {
+    TC sF[3][5];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sF[d][v] = TC(0);
+#pragma unroll
+    for (int qp = 0; qp < 8; ++qp) {
+      TC c[5];
+      eval3d<TC>(c0, s, (qp & 1) ? oo[0] : -oo[0], (qp & 2) ? oo[1] : -oo[1],
+                 (qp & 4) ? oo[2] : -oo[2], c);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        TC F[5];
+        phys_flux3d<TC>(G, c, d, F, err);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sF[d][v] += F[v];
+      }
+    }
+    const TC hd[3] = {dx, dy, dz};
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) rs[3 * v + d] = TC(1.5) / (hd[d] * hd[d]) * sF[d][v];
+  }
+
+  // ---- faces, one orientation at a time
+  const TC hd[3] = {dx, dy, dz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int FX = TX + (d == 0), FY = TY + (d == 1), FZ = TZ + (d == 2);
+    const int NFACE = FX * FY * FZ;
+    const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+    for (int e = tid; e < 4 * NFACE; e += NT) {
+      const int f = e >> 2, g = e & 3;
+      const int fz = f / (FX * FY), fr = f - fz * (FX * FY);
+      const int fy = fr / FX, fx = fr - fy * FX;
+      // the cell on the + side of the face has tile coordinates (fx, fy, fz),
+      // i.e. halo-1 coordinates (fx+1, fy+1, fz+1); the - side is one step back
+      // along d
+      const int r1r = ((fz + 1) * R1Y + (fy + 1)) * R1X + (fx + 1);
+      const int step = d == 0 ? 1 : (d == 1 ? R1X : R1X * R1Y);
+      const int r1l = r1r - step;
+      TC pl[3], pr[3];
+      pl[d] = hh[d];
+      pr[d] = -hh[d];
+      const TC a = (g & 2) ? oo[e1] : -oo[e1], b = (g & 1) ? oo[e2] : -oo[e2];
+      pl[e1] = pr[e1] = a;
+      pl[e2] = pr[e2] = b;
+      TC cl0[5], cr0[5], sl[15], sr[15], cl[5], cr[5], F[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) { cl0[v] = s_c0[v * R1 + r1l]; cr0[v] = s_c0[v * R1 + r1r]; }
+#pragma unroll
+      for (int k = 0; k < 15; ++k) { sl[k] = s_sl[k * R1 + r1l]; sr[k] = s_sl[k * R1 + r1r]; }
+      eval3d<TC>(cl0, sl, pl[0], pl[1], pl[2], cl);
+      eval3d<TC>(cr0, sr, pr[0], pr[1], pr[2], cr);
+      face_flux3d<TC>(G, d, cl, cr, F, err);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s_f[(v * 4 + g) * FMAX + f] = F[v];
+    }
+    __syncthreads();
+    {
+      const int fm = (lz * FY + ly) * FX + lx;
+      const int fp = fm + (d == 0 ? 1 : (d == 1 ? FX : FX * FY));
+      const TC c0f = TC(0.25) / hd[d];
+      const TC csf = TC(1.5) / (hd[d] * hd[d]);
+      const TC ce1 = TC(0.86602540378443864676) / (hd[e1] * hd[d]);
+      const TC ce2 = TC(0.86602540378443864676) / (hd[e2] * hd[d]);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        TC m0 = s_f[(v * 4 + 0) * FMAX + fm], m1 = s_f[(v * 4 + 1) * FMAX + fm];
+        TC m2 = s_f[(v * 4 + 2) * FMAX + fm], m3 = s_f[(v * 4 + 3) * FMAX + fm];
+        TC p0 = s_f[(v * 4 + 0) * FMAX + fp], p1 = s_f[(v * 4 + 1) * FMAX + fp];
+        TC p2 = s_f[(v * 4 + 2) * FMAX + fp], p3 = s_f[(v * 4 + 3) * FMAX + fp];
+        TC Sm = (m0 + m1) + (m2 + m3), Sp = (p0 + p1) + (p2 + p3);
+        TC Dm1 = (m2 + m3) - (m0 + m1), Dp1 = (p2 + p3) - (p0 + p1);
+        TC Dm2 = (m1 + m3) - (m0 + m2), Dp2 = (p1 + p3) - (p0 + p2);
+        rc0[v] -= (Sp - Sm) * c0f;
+        rs[3 * v + d] -= csf * (Sp + Sm);
+        rs[3 * v + e1] -= ce1 * (Dp1 - Dm1);
+        rs[3 * v + e2] -= ce2 * (Dp2 - Dm2);
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- Runge-Kutta combination
+  const int gi = i0 + lx, gj = j0 + ly, gk = k0 + lz;
+  const bool owner = gi < nx && gj < ny && gk < nz;
+  const size_t gc = (size_t)s_gz[lz + 2] + s_gy[ly + 2] + s_gx[lx + 2];
+  const double dt = s_dt;
+  const TC dtc = (TC)dt;
+  double o0[5];
+  TC os[15];
+  if (STAGE == 1) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) o0[v] = A.in.c0[v * ncell + gc] + dt * (double)rc0[v];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) os[k] = s[k] + dtc * rs[k];
+  } else {
+    TC sn[15];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) sn[k] = (TC)A.base.sl[k * ncell + gc];
+    if (A.limiter) {
+      TC c[5], W[5], Wn[6][5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) c[v] = (TC)A.base.c0[v * ncell + gc];
+      prims3d<TC>(G, c, W, err);
+      const size_t nb[6] = {(size_t)s_gz[lz + 2] + s_gy[ly + 2] + s_gx[lx + 1],
+                            (size_t)s_gz[lz + 2] + s_gy[ly + 2] + s_gx[lx + 3],
+                            (size_t)s_gz[lz + 2] + s_gy[ly + 1] + s_gx[lx + 2],
+                            (size_t)s_gz[lz + 2] + s_gy[ly + 3] + s_gx[lx + 2],
+                            (size_t)s_gz[lz + 1] + s_gy[ly + 2] + s_gx[lx + 2],
+                            (size_t)s_gz[lz + 3] + s_gy[ly + 2] + s_gx[lx + 2]};
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) c[v] = (TC)A.base.c0[v * ncell + nb[k]];
+        prims3d<TC>(G, c, Wn[k], err);
+      }
+      limit_cell3d<TC>(G, hh, W, Wn, sn);
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+      o0[v] = 0.5 * A.base.c0[v * ncell + gc] + 0.5 * (A.in.c0[v * ncell + gc] + dt * (double)rc0[v]);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) os[k] = TC(0.5) * sn[k] + TC(0.5) * (s[k] + dtc * rs[k]);
+  }
+  if (owner) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) A.out.c0[v * ncell + gc] = o0[v];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) A.out.sl[k * ncell + gc] = (TS)os[k];
+  }
+
+  if (STAGE == 2) {
+    double sp = 0.0;
+    if (owner) {
+      TC c[5], W[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) c[v] = (TC)o0[v];
+      prims3d<TC>(G, c, W, err);
+      TC cs = sqrt(G.g * W[4] / W[0]);
+      sp = (double)((fabs(W[1]) + cs) / dx + (fabs(W[2]) + cs) / dy + (fabs(W[3]) + cs) / dz);
+      if (!(sp >= 0.0)) { err |= ERR_NONPHYS; sp = 0.0; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double t = __shfl_xor_sync(0xffffffffu, sp, o);
+      sp = t > sp ? t : sp;
+    }
+    if ((tid & 31) == 0) s_red[tid >> 5] = sp;
+    if (err) atomicOr(&s_err, err);
+    __syncthreads();
+    if (tid == 0) {
+      double m = 0.0;
+      for (int w = 0; w < NT / 32; ++w) m = s_red[w] > m ? s_red[w] : m;
+      Ctl* ctl = A.ctl;
+      atomicMax(&ctl->vmax_next, (unsigned long long)__double_as_longlong(m));
+      if (s_err) atomicOr(&ctl->err, s_err);
+      __threadfence();
+      unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+      unsigned tk = atomicAdd(&ctl->ticket, 1u);
+      if (tk == nblk - 1) {
+        __threadfence();
+        double vm = __longlong_as_double((long long)atomicAdd(&ctl->vmax_next, 0ull));
+        ctl->vmax_cur = vm;
+        ctl->vmax_next = 0ull;
+        ctl->t += dt;
+        ctl->dt_last = dt;
+        if (ctl->dt_hist && ctl->step < ctl->hist_cap) ctl->dt_hist[ctl->step] = dt;
+        ctl->step += 1;
+        if (!(vm > 0.0)) ctl->err |= ERR_NONPHYS;
+        __threadfence();
+        ctl->ticket = 0u;
+      }
+    }
+  } else {
+    if (err) atomicOr(&s_err, err);
+    __syncthreads();
+    if (tid == 0 && s_err) atomicOr(&A.ctl->err, s_err);
+  }
+}
+
+}  // namespace dgk
