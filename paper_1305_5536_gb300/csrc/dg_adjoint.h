@@ -21,6 +21,8 @@ struct AdjointStore {
   // work buffers of the reverse sweep (allocated on first use)
   void* work = nullptr;
   size_t work_bytes = 0;
+  long work_ncell = 0;
+  int work_fp32 = -1;
 };
 
 struct AdjointCall {

@@ -102,18 +102,14 @@ __device__ __forceinline__ void pressure_fn(const Gas<T>& G, T p, T rK, T pK, T 
   }
 }
 
-template <class T, int NT>
-__device__ __forceinline__ void exact_flux(const Gas<T>& G, T rL, T uL, T pL, const T* vtL, T rR,
-                                           T uR, T pR, const T* vtR, T* F, unsigned& err) {
-  if (!(rL > T(0) && pL > T(0) && rR > T(0) && pR > T(0))) {
-    err |= ERR_NONPHYS;
-    for (int q = 0; q < 3 + NT; ++q) F[q] = T(0);
-    return;
-  }
-  const T cL = rsqrtv(G.g * pL / rL), cR = rsqrtv(G.g * pR / rR);
+// Star-region pressure p* of the Riemann problem (rho, u, p)_L | (rho, u, p)_R:
+// root of f_L(p) + f_R(p) + (u_R - u_L) by Newton iteration from the adaptive
+// PVRS / two-rarefaction / two-shock first guess.  cL, cR are the sound speeds.
+template <class T>
+__device__ __forceinline__ T exact_pstar(const Gas<T>& G, T rL, T uL, T pL, T cL, T rR, T uR, T pR,
+                                         T cR, unsigned& err) {
   const T du = uR - uL;
   if (G.two_gm1 * (cL + cR) <= du) err |= ERR_VACUUM;
-  // first guess: PVRS inside its range, else two-rarefaction or two-shock
   T pv = T(0.5) * (pL + pR) - T(0.125) * du * (rL + rR) * (cL + cR);
   pv = pv > T(0) ? pv : T(0);
   const T pmin = pL < pR ? pL : pR, pmax = pL < pR ? pR : pL;
@@ -143,6 +139,19 @@ __device__ __forceinline__ void exact_flux(const Gas<T>& G, T rL, T uL, T pL, co
     if (change < Prec<T>::newton_tol) { conv = true; break; }
   }
   if (!conv) err |= ERR_NEWTON;
+  return p;
+}
+
+template <class T, int NT>
+__device__ __forceinline__ void exact_flux(const Gas<T>& G, T rL, T uL, T pL, const T* vtL, T rR,
+                                           T uR, T pR, const T* vtR, T* F, unsigned& err) {
+  if (!(rL > T(0) && pL > T(0) && rR > T(0) && pR > T(0))) {
+    err |= ERR_NONPHYS;
+    for (int q = 0; q < 3 + NT; ++q) F[q] = T(0);
+    return;
+  }
+  const T cL = rsqrtv(G.g * pL / rL), cR = rsqrtv(G.g * pR / rR);
+  const T p = exact_pstar(G, rL, uL, pL, cL, rR, uR, pR, cR, err);
   T fL, dfL, fR, dfR;
   pressure_fn(G, p, rL, pL, cL, fL, dfL);
   pressure_fn(G, p, rR, pR, cR, fR, dfR);

@@ -267,5 +267,39 @@ def totals_noalloc(u, eq="euler", dim=2, n=(64, 64), box=(1.0, 1.0, 1.0), stream
     return out
 
 
+_ROLLOUT = None
+
+
+def _rollout_fn():
+    global _ROLLOUT
+    if _ROLLOUT is None:
+        import torch
+
+        class DGRollout(torch.autograd.Function):
+            """u_T = nsteps GPU DG steps from u_0 (interchange layout, float64 CUDA
+            tensor).  The forward pass records the trajectory (checkpoints every
+            cfg.ckpt_every steps and the time steps, which are then held fixed);
+            the backward pass is the checkpointed adjoint of the library."""
+
+            @staticmethod
+            def forward(ctx, u0, solver, nsteps, dt):
+                solver.set_state(u0.detach().contiguous())
+                solver.record(nsteps, dt)
+                ctx.solver = solver
+                return solver.get_state(device=u0.device)
+
+            @staticmethod
+            def backward(ctx, g):
+                return ctx.solver.adjoint(g.contiguous()), None, None, None
+
+        _ROLLOUT = DGRollout
+    return _ROLLOUT
+
+
+def rollout(u0, solver, nsteps, dt=0.0):
+    """Differentiable rollout: gradients of an objective of u_T flow back to u_0."""
+    return _rollout_fn().apply(u0, solver, nsteps, dt)
+
+
 def batch(configs, stream=None):
     return DGSolver(configs=configs, stream=stream)

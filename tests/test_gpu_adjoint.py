@@ -1,0 +1,167 @@
+"""Adjoint (vector-Jacobian products) of the 2D Euler DG step on the GPU.
+
+Checked against the oracle's FP64 tangent model (dot-product identity
+<J^T lam, d> = <lam, J d>), against the full Jacobian built column by column
+from the oracle on a tiny grid, and against central finite differences of the
+GPU forward map over a checkpointed multi-step rollout with the time steps held
+fixed.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1305_5536_gb300 import dg, ics
+
+pytestmark = pytest.mark.gpu
+
+
+def _state(n, seed=3):
+    f = lambda X, Y: (1 + 0.2 * np.sin(2 * np.pi * (X + Y) + 0.31),
+                      0.5 + 0.2 * np.sin(2 * np.pi * X + 0.47),
+                      -0.3 + 0.2 * np.cos(2 * np.pi * Y + 0.23),
+                      1 + 0.1 * np.sin(2 * np.pi * (X - 2 * Y) + 0.11))
+    return ics.add_slope_noise(ics.project_2d(f, n), 0, 2, 0.05, np.random.default_rng(seed))
+
+
+def _vjp(n, u, lam, dt, prec, limiter, box=(1.0, 0.9)):
+    import torch
+    s = dg.DGSolver("euler", 2, n, box=box + (1.0,), precision=prec, limiter=limiter)
+    ud = torch.from_numpy(u).cuda()
+    ld = torch.from_numpy(lam).cuda()
+    out = s.adjoint_step(ld, ud, dt)
+    torch.cuda.synchronize()
+    s.close()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+@pytest.mark.parametrize("n", [(12, 10), (37, 29), (5, 3)])
+@pytest.mark.parametrize("limiter", [0, 1])
+def test_adjoint_step_dot_product(prec, tol, n, limiter):
+    u = _state(n)
+    P = O.Problem(O.EULER, 2, n, box=(1.0, 0.9), limiter=limiter)
+    dt = 0.5 * P.cfl_dt(u)[0]
+    rng = np.random.default_rng(7)
+    lam = rng.standard_normal(u.shape)
+    d = rng.standard_normal(u.shape)
+    _, Jd, fl = P.tangent_step(u, d, dt)
+    assert fl == 0
+    JTl = _vjp(n, u, lam, dt, prec, limiter)
+    a, b = float((JTl * d).sum()), float((lam * Jd).sum())
+    scale = float(np.abs(JTl * d).sum())
+    if prec == "fp32" and limiter:
+        # The limiter's derivative jumps where its min/max or min(1, psi) switches
+        # branch; FP32 rounding of nearly tied neighbour values flips the branch in
+        # a few cells, so only rough agreement is expected (FP64 is exact above).
+        tol = 0.1
+    assert abs(a - b) < tol * scale, (a, b)
+
+
+@pytest.mark.parametrize("limiter", [0, 1])
+def test_adjoint_step_full_jacobian_tiny(limiter):
+    n = (4, 4)
+    u = _state(n)
+    P = O.Problem(O.EULER, 2, n, box=(1.0, 0.9), limiter=limiter)
+    dt = 0.5 * P.cfl_dt(u)[0]
+    N = u.size
+    J = np.zeros((N, N))
+    for k in range(N):
+        e = np.zeros(N)
+        e[k] = 1.0
+        _, col, _ = P.tangent_step(u, e.reshape(u.shape), dt)
+        J[:, k] = col.ravel()
+    rng = np.random.default_rng(8)
+    for _ in range(3):
+        lam = rng.standard_normal(u.shape)
+        ref = (J.T @ lam.ravel()).reshape(u.shape)
+        got = _vjp(n, u, lam, dt, "fp64", limiter)
+        np.testing.assert_allclose(got, ref, atol=1e-12 * np.abs(ref).max())
+
+
+def _objective_grad(uT, target, h):
+    """J = 1/2 int (rho_h - rho_target)^2 over the box, exact on P1 polynomials:
+    V sum [(d avg)^2 + dx^2/12 (d rho_x)^2 + dy^2/12 (d rho_y)^2]; returns (J, dJ/du_T)."""
+    V = h[0] * h[1]
+    w = np.array([1.0, h[0] ** 2 / 12, h[1] ** 2 / 12])
+    d = uT[0:3] - target[0:3]
+    J = 0.5 * V * float((w[:, None, None] * d * d).sum())
+    g = np.zeros_like(uT)
+    g[0:3] = V * w[:, None, None] * d
+    return J, g
+
+
+def _forward_fixed(n, u0, dts, prec, limiter):
+    s = dg.DGSolver("euler", 2, n, precision=prec, limiter=limiter)
+    s.set_state(u0)
+    for dt in dts:
+        s.step(1, dt=dt)
+    s.sync()
+    out = s.get_state()
+    s.close()
+    return out
+
+
+def test_adjoint_rollout_vs_central_differences_and_oracle():
+    """Smooth random density perturbation (the adjoint workload, reduced to 48x48
+    and 12 steps), limiter off as in that workload (its uniform velocity and
+    pressure would put every cell on a tie of the limiter's min/max), objective =
+    L2 misfit of the final density against a target, checkpoints every 5 steps."""
+    limiter = 0
+    import torch
+    n = (48, 48)
+    u0, delta = ics.euler2d_random_density(n, kmax=6)
+    h = (1.0 / n[0], 1.0 / n[1])
+    nsteps = 12
+    s = dg.DGSolver("euler", 2, n, precision="fp64", limiter=limiter, ckpt_every=5)
+    s.set_state(u0)
+    s.record(nsteps)
+    uT = s.get_state()
+    target = ics.euler2d_random_density(n, kmax=6, seed=99)[0]
+    J0, gT = _objective_grad(uT, target, h)
+    g0 = s.adjoint(torch.from_numpy(gT).cuda()).cpu().numpy()
+    # the recorded time steps (held fixed), from the oracle's Courant rule
+    P = O.Problem(O.EULER, 2, n, limiter=limiter)
+    _, dts, _ = P.run(u0, nsteps, cfl=0.3)
+    np.testing.assert_allclose(_forward_fixed(n, u0, dts, "fp64", limiter), uT, rtol=0,
+                               atol=1e-12 * np.abs(uT).max())
+    rng = np.random.default_rng(21)
+    d = rng.standard_normal(u0.shape) * 1e-2
+    d[1:3] *= 10.0
+    gd = float((g0 * d).sum())
+    # central differences of the GPU forward map with the same time steps
+    eps = 1e-5
+    Jp, _ = _objective_grad(_forward_fixed(n, u0 + eps * d, dts, "fp64", limiter), target, h)
+    Jm, _ = _objective_grad(_forward_fixed(n, u0 - eps * d, dts, "fp64", limiter), target, h)
+    fd = (Jp - Jm) / (2 * eps)
+    assert abs(gd - fd) < 1e-6 * abs(fd), (gd, fd)
+    # the oracle's own FP64 tangent through the same steps
+    u, du = u0.copy(), d.copy()
+    for dt in dts:
+        u, du, fl = P.tangent_step(u, du, dt)
+        assert fl == 0
+    ref = float((gT * du).sum())
+    assert abs(gd - ref) < 1e-10 * abs(ref), (gd, ref)
+    s.close()
+
+
+def test_autograd_rollout_fp32_gradient():
+    import torch
+    n = (32, 32)
+    u0, _ = ics.euler2d_random_density(n, kmax=4)
+    s = dg.DGSolver("euler", 2, n, precision="fp32", limiter=0, ckpt_every=3)
+    x = torch.from_numpy(u0).cuda().requires_grad_(True)
+    uT = dg.rollout(x, s, 7)
+    loss = (uT[0] ** 2).sum()
+    loss.backward()
+    g = x.grad.double().cpu().numpy()
+    # central differences of the FP64 forward with the recorded time steps
+    P = O.Problem(O.EULER, 2, n, limiter=0)
+    _, dts, _ = P.run(u0, 7, cfl=0.3)
+    rng = np.random.default_rng(5)
+    d = rng.standard_normal(u0.shape) * 1e-2
+    eps = 1e-4
+    f = lambda u: float((_forward_fixed(n, u, dts, "fp64", 0)[0] ** 2).sum())
+    fd = (f(u0 + eps * d) - f(u0 - eps * d)) / (2 * eps)
+    assert abs(float((g * d).sum()) - fd) < 2e-4 * abs(fd)
