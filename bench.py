@@ -38,7 +38,25 @@ WORKLOADS = {
         "limiter, CFL 0.3")),
     "kh3d_256": dict(eq="euler", dim=3, n=(256, 256, 256), desc=(
         "3D Euler Kelvin-Helmholtz shear layer 256^3, exact Riemann, limiter, CFL 0.3")),
+    "mhd_batch64": dict(eq="mhd", dim=2, n=None, desc=(
+        "64 independent 2D ideal-MHD problems, N log-uniform in [32, 512] (seeded), "
+        "random-phase smooth v and div-free B, one persistent launch per step, CFL 0.3")),
 }
+
+
+def _workload_state(W):
+    """(initial interchange state, total cells, solver configs or None)."""
+    from paper_1305_5536_gb300 import dg, ics
+    if W["n"] is None:
+        sizes, us = ics.mhd_batch()
+        return np.concatenate([u.ravel() for u in us]), sum(N * N for N in sizes), sizes
+    if W["eq"] == "mhd":
+        u0 = ics.orszag_tang(W["n"])
+    elif W["dim"] == 3:
+        u0 = ics.kh3d(W["n"])
+    else:
+        u0 = ics.euler2d_wave(W["n"])
+    return u0, int(np.prod(W["n"])), None
 
 
 def _peaks():
@@ -149,13 +167,7 @@ def run_gpu(args):
     if ws > 1:
         tdist.init_process_group("nccl")
     W = WORKLOADS[args.workload]
-    if W["eq"] == "mhd":
-        u0 = ics.orszag_tang(W["n"])
-    elif W["dim"] == 3:
-        u0 = ics.kh3d(W["n"])
-    else:
-        u0 = ics.euler2d_wave(W["n"])
-    ncell = int(np.prod(W["n"]))
+    u0, ncell, sizes = _workload_state(W)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -164,8 +176,14 @@ def run_gpu(args):
             tdist.barrier()
         torch.cuda.synchronize()
 
+    def new_solver(prec):
+        if sizes is not None:
+            return dg.DGSolver(configs=[dg.make_config(W["eq"], 2, (N, N), precision=prec)
+                                        for N in sizes])
+        return dg.DGSolver(W["eq"], W["dim"], W["n"], precision=prec, cfl=0.3)
+
     def measure(prec, K, Wm, with_clock):
-        s = dg.DGSolver(W["eq"], W["dim"], W["n"], precision=prec, cfl=0.3)
+        s = new_solver(prec)
         s.set_state(u0)
         for _ in range(Wm):
             flush.fill_(1.0)
@@ -236,6 +254,8 @@ def run_gpu(args):
     achieved = r32["bytes"][k] / (avg_ms * 1e-3) / 1e9
     kname = ("stage2d_kernel<%s,float,float,stage%d>" % (W["eq"], k + 1) if W["dim"] == 2
              else "stage3d_kernel<float,float,stage%d>" % (k + 1))
+    if sizes is not None:
+        kname = "batch2d_kernel<%s,float,float> (both stages)" % W["eq"]
     traffic = _traffic(kname, args.workload)
     v64 = ws * ncell / (r64["ms_per_step"] * 1e-3)
     out = {
@@ -251,7 +271,7 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (analytic initial condition projected onto the P1 bases)",
-        "config": {"workload": W["desc"], "grid": list(W["n"]),
+        "config": {"workload": W["desc"], "grid": list(W["n"]) if W["n"] else sizes,
                    "precision": "FP32 arithmetic + FP32 derivative coefficients, FP64 averages",
                    "l2": "flushed (512 MiB write) before every timed step",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -283,9 +303,21 @@ ORACLE_MAX_CELLS = 300_000
 
 
 def _oracle_sample(workload, u0):
-    """(oracle problem, state, description) of the bounded CPU sample."""
+    """[(oracle problem, state)], description, cells per sweep: the bounded CPU
+    sample of a workload (whole grid, a periodic sub-box, or a few problems of a
+    batch)."""
     import oracle as O
     W = WORKLOADS[workload]
+    if W["n"] is None:
+        from paper_1305_5536_gb300 import ics
+        sizes, us = ics.mhd_batch()
+        items, cells = [], 0
+        for N, u in zip(sizes, us):
+            if cells + N * N > ORACLE_MAX_CELLS:
+                continue
+            items.append((O.Problem(O.MHD, 2, (N, N)), u))
+            cells += N * N
+        return items, "%d of the batch's problems (%d cells)" % (len(items), cells), cells
     n = list(W["n"])
     box = [1.0] * W["dim"]
     desc = "whole grid"
@@ -297,18 +329,22 @@ def _oracle_sample(workload, u0):
         u0 = np.ascontiguousarray(u0[(slice(None),) + sl])
         desc = "periodic %s sub-box of the same cells" % "x".join(map(str, n))
     P = O.Problem(O.MHD if W["eq"] == "mhd" else O.EULER, W["dim"], n, box=box)
-    return P, u0, desc, int(np.prod(n))
+    return [(P, u0)], desc, int(np.prod(n))
+
+
+def _oracle_sweep(items, dts):
+    return [(P, P.step(u, dt)[0]) for (P, u), dt in zip(items, dts)]
 
 
 def cpu_baseline(workload, u0, budget_s=12.0, max_steps=50):
     """The CPU oracle, as it stands, on one host core: SSP-RK2 steps of the same
-    workload (or of a periodic sub-box of it) until ~budget_s of CPU time."""
-    P, u, desc, ncell = _oracle_sample(workload, u0)
-    dt = P.cfl_dt(u)[0]
+    workload (or of a bounded part of it) until ~budget_s of CPU time."""
+    items, desc, ncell = _oracle_sample(workload, u0)
+    dts = [P.cfl_dt(u)[0] for P, u in items]
     n = 0
     t0 = time.perf_counter()
     while n < max_steps:
-        u, _ = P.step(u, dt)
+        items = _oracle_sweep(items, dts)
         n += 1
         if time.perf_counter() - t0 > budget_s:
             break
@@ -321,21 +357,15 @@ def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
         return
-    from paper_1305_5536_gb300 import ics
     W = WORKLOADS[args.workload]
-    if W["eq"] == "mhd":
-        u0 = ics.orszag_tang(W["n"])
-    elif W["dim"] == 3:
-        u0 = ics.kh3d(W["n"])
-    else:
-        u0 = ics.euler2d_wave(W["n"])
-    P, u, desc, ncell = _oracle_sample(args.workload, u0)
-    dt = P.cfl_dt(u)[0]
+    u0, _, _ = _workload_state(W)
+    items, desc, ncell = _oracle_sample(args.workload, u0)
+    dts = [P.cfl_dt(u)[0] for P, u in items]
     for _ in range(args.warmup):
-        u, _ = P.step(u, dt)
+        items = _oracle_sweep(items, dts)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        u, _ = P.step(u, dt)
+        items = _oracle_sweep(items, dts)
     el = time.perf_counter() - t0
     v = args.steps * ncell / el
     print(json.dumps({
@@ -343,7 +373,7 @@ def run_reference(args):
         "value": v, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": W["desc"], "grid": list(W["n"])},
+        "config": {"workload": W["desc"], "grid": list(W["n"]) if W["n"] else "batch"},
         "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
                          "sample": "%d SSP-RK2 steps, %s" % (args.steps, desc)},
         "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,

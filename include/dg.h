@@ -182,12 +182,14 @@ dg_status dg_totals_noalloc(const dg_config* cfg, const double* u, double* out,
 dg_status dg_profile(dg_ctx* ctx, int enable);
 
 /* Totals of the recorded kernel times: ms[k] and launches[k] for k = 0 (stage 1)
- * and 1 (stage 2 incl. the fused time-step reduction).  Synchronises. */
+ * and 1 (stage 2 incl. the fused time-step reduction).  A batch of 2D problems
+ * runs both stages in one launch per step, counted under k = 1.  Synchronises. */
 dg_status dg_profile_read(dg_ctx* ctx, double ms[2], long long launches[2]);
 
 /* Algorithmic DRAM bytes of one stage-kernel launch on the whole grid (all
  * problems): stage 1 reads and writes one state, stage 2 reads two and writes
- * one.  Used for roofline figures. */
+ * one (a batch of 2D problems: 0 for stage 1, both stages for stage 2).  Used for
+ * roofline figures. */
 double dg_stage_bytes(const dg_ctx* ctx, int stage);
 
 #ifdef __cplusplus

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdg.so")
 SOURCES = ["dg_capi.cu", "dg_misc.cu", "dg_k2d.cu", "dg_k3d.cu", "dg_adjoint.cu",
-           "dg_noalloc.cu"]
+           "dg_noalloc.cu", "dg_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

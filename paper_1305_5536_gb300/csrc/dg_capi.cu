@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <string>
@@ -16,6 +17,7 @@
 
 #include "../../include/dg.h"
 #include "dg_adjoint.h"
+#include "dg_batch.h"
 #include "dg_internal.h"
 
 using namespace dgk;
@@ -67,6 +69,13 @@ struct dg_ctx {
   std::vector<EvPair> evs;
   // adjoint recording
   AdjointStore adj;
+  // batched 2D problems: one persistent launch per step over a tile work list
+  bool batch2d = false;
+  BatchProb* btab[3] = {nullptr, nullptr, nullptr};  // per tile variant
+  int btiles[3] = {0, 0, 0};
+  unsigned* bar = nullptr;
+  long long spin_limit = 1LL << 24;
+  int extra_arrivals = 0;
 };
 
 namespace {
@@ -185,6 +194,29 @@ void free_graphs(dg_ctx* c) {
 // stage launches
 // ---------------------------------------------------------------------------
 template <class TS>
+cudaError_t launch_batch_step_t(dg_ctx* c, int a, int b, double dtov) {
+  const int v = c->variant < 0 ? 0 : c->variant;
+  BatchArgs<TS> B;
+  B.probs = c->btab[v];
+  B.nprob = (int)c->probs.size();
+  B.ntiles = c->btiles[v];
+  B.gamma = c->gamma;
+  B.cfl = c->cfl;
+  B.dt_override = dtov;
+  B.limiter = c->limiter;
+  const int bufs[3] = {a, 1, b};
+  for (int k = 0; k < 3; ++k) {
+    B.c0[k] = c->c0[bufs[k]];
+    B.sl[k] = reinterpret_cast<TS*>(c->sl[bufs[k]]);
+  }
+  B.ctl = c->ctl;
+  B.bar = c->bar;
+  B.spin_limit = c->spin_limit;
+  B.barrier_extra = c->extra_arrivals;
+  return launch_batch2d(c->eq, v, B, c->launch_stream, nullptr);
+}
+
+template <class TS>
 cudaError_t launch_stage_t(dg_ctx* c, int stage, int in, int base, int out, double dtov) {
   for (size_t ip = 0; ip < c->probs.size(); ++ip) {
     const Prob& p = c->probs[ip];
@@ -223,12 +255,25 @@ cudaError_t launch_stage(dg_ctx* c, int stage, int in, int base, int out, double
 
 // One SSP-RK2 step from buffer `a` into buffer `b` (buffer 1 holds V^1).
 cudaError_t launch_step(dg_ctx* c, int a, int b, double dtov) {
+  if (c->batch2d)
+    return c->fp32 ? launch_batch_step_t<float>(c, a, b, dtov) : launch_batch_step_t<double>(c, a, b, dtov);
   cudaError_t e = launch_stage(c, 1, a, a, 1, dtov);
   if (e != cudaSuccess) return e;
   return launch_stage(c, 2, 1, a, b, dtov);
 }
 
 cudaError_t launch_step_profiled(dg_ctx* c, int a, int b, double dtov) {
+  if (c->batch2d) {
+    EvPair ev;
+    ev.kind = 1;
+    cudaEventCreate(&ev.a);
+    cudaEventCreate(&ev.b);
+    cudaEventRecord(ev.a, c->stream);
+    cudaError_t e = launch_step(c, a, b, dtov);
+    cudaEventRecord(ev.b, c->stream);
+    c->evs.push_back(ev);
+    return e;
+  }
   for (int s = 1; s <= 2; ++s) {
     EvPair ev;
     ev.kind = s - 1;
@@ -284,6 +329,17 @@ dg_status check_err(dg_ctx* c) {
   if (s != DG_OK) return s;
   for (size_t p = 0; p < c->probs.size(); ++p) {
     unsigned e = c->ctl_host[p].err;
+    if (e & ERR_TIMEOUT) {
+      // leave the context usable: clear the barrier and the error words (the
+      // state of the failed step is unreliable; set it again to continue)
+      CK(c, cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), c->stream));
+      for (size_t q = 0; q < c->probs.size(); ++q)
+        CK(c, cudaMemsetAsync((char*)(c->ctl + q) + offsetof(Ctl, err), 0, sizeof(unsigned),
+                              c->stream));
+      CK(c, cudaStreamSynchronize(c->stream));
+      return fail(c, DG_ETIMEOUT, "grid barrier of the batched step timed out (step %lld)",
+                  (long long)c->ctl_host[p].step);
+    }
     if (e)
       return fail(c, DG_ENONPHYS,
                   "problem %zu: device error word 0x%x (1 non-physical state, 2 Riemann vacuum, "
@@ -306,6 +362,7 @@ dg_status init_cfl_t(dg_ctx* c) {
 
 dg_status reset_ctl_and_cfl(dg_ctx* c) {
   CK(c, launch_ctl_reset(c->ctl, (int)c->probs.size(), c->stream));
+  if (c->bar) CK(c, cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), c->stream));
   dg_status s = c->fp32 ? init_cfl_t<float>(c) : init_cfl_t<double>(c);
   if (s != DG_OK) return s;
   CK(c, launch_ctl_commit(c->ctl, (int)c->probs.size(), c->stream));
@@ -384,8 +441,7 @@ dg_status autotune(dg_ctx* c) {
     float tot = 0.0f;
     for (int rep = 0; rep < 4; ++rep) {
       CK(c, cudaEventRecord(e0, c->stream));
-      CK(c, launch_stage(c, 1, c->cur, c->cur, 1, dt));
-      CK(c, launch_stage(c, 2, 1, c->cur, c->nxt, dt));
+      CK(c, launch_step(c, c->cur, c->nxt, dt));
       CK(c, cudaEventRecord(e1, c->stream));
       CK(c, cudaEventSynchronize(e1));
       float ms = 0.0f;
@@ -446,6 +502,48 @@ static dg_status get_state_t(dg_ctx* c, double* dst, int on_device) {
 
 void dgk::set_global_error(const std::string& msg) { g_err = msg; }
 
+namespace {
+
+// Tile work lists of a 2D batch, one per compiled tile shape, and the barrier.
+dg_status build_batch(dg_ctx* c) {
+  c->batch2d = true;
+  for (int v = 0; v < 3; ++v) {
+    const int tx = batch2d_tile_x(c->fp32, v), ty = batch2d_tile_y(c->fp32, v);
+    std::vector<BatchProb> tab;
+    int begin = 0;
+    for (const Prob& p : c->probs) {
+      BatchProb b{};
+      b.nx = p.nx;
+      b.ny = p.ny;
+      b.tiles_x = (p.nx + tx - 1) / tx;
+      b.ntiles = b.tiles_x * ((p.ny + ty - 1) / ty);
+      b.tile_begin = begin;
+      b.ncell = p.ncell;
+      b.dx = p.dx;
+      b.dy = p.dy;
+      b.c0_off = (long)p.c0_off;
+      b.sl_off = (long)p.sl_off;
+      begin += b.ntiles;
+      tab.push_back(b);
+    }
+    c->btiles[v] = begin;
+    CK(c, cudaMalloc(&c->btab[v], tab.size() * sizeof(BatchProb)));
+    CK(c, cudaMemcpy(c->btab[v], tab.data(), tab.size() * sizeof(BatchProb), cudaMemcpyHostToDevice));
+  }
+  CK(c, cudaMalloc(&c->bar, 2 * sizeof(unsigned)));
+  CK(c, cudaMemset(c->bar, 0, 2 * sizeof(unsigned)));
+  // test hook (no GPU fault, no hang): the barrier expects one CTA more than is
+  // launched, so every wait runs out after a short bounded spin
+  const char* t = getenv("DG_TEST_BARRIER_TIMEOUT");
+  if (t && atoi(t) > 0) {
+    c->extra_arrivals = 1;
+    c->spin_limit = 20000;
+  }
+  return DG_OK;
+}
+
+}  // namespace
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -505,6 +603,7 @@ static dg_status init_common(const dg_config* cfgs, int nprob, void* stream, dg_
     c->probs.push_back(p);
   }
   dg_status s = alloc_ctx(c);
+  if (s == DG_OK && nprob > 1 && c->dim == 2) s = build_batch(c);
   if (s != DG_OK) {
     g_err = c->err;
     dg_destroy(c);
@@ -539,6 +638,8 @@ void dg_destroy(dg_ctx* c) {
   cudaFree(c->scratch);
   cudaFree(c->ctl);
   cudaFree(c->totals_dev);
+  for (int v = 0; v < 3; ++v) cudaFree(c->btab[v]);
+  cudaFree(c->bar);
   if (c->ctl_host) cudaFreeHost(c->ctl_host);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
@@ -665,7 +766,8 @@ dg_status dg_profile_read(dg_ctx* c, double ms[2], long long launches[2]) {
     float t = 0.0f;
     CK(c, cudaEventElapsedTime(&t, e.a, e.b));
     ms[e.kind] += t;
-    launches[e.kind] += (long long)c->probs.size();
+    // a batched 2D step is one launch; otherwise every problem is launched
+    launches[e.kind] += c->batch2d ? 1 : (long long)c->probs.size();
   }
   return DG_OK;
 }
@@ -673,6 +775,8 @@ dg_status dg_profile_read(dg_ctx* c, double ms[2], long long launches[2]) {
 double dg_stage_bytes(const dg_ctx* c, int stage) {
   if (!c) return 0.0;
   double per = (double)c->nv * 8.0 + (double)c->ns * (c->fp32 ? 4.0 : 8.0);
+  if (c->batch2d)  // one fused launch per step, reported as stage 2
+    return (stage == 1 ? 0.0 : 5.0) * per * (double)c->ncell_total;
   return (stage == 1 ? 2.0 : 3.0) * per * (double)c->ncell_total;
 }
 

@@ -201,8 +201,12 @@ __device__ __forceinline__ void face_flux2d(const Gas<TC>& G, int dir, const TC*
   else { F[1] = Ff[2]; F[2] = Ff[1]; }
 }
 
+// One tile of one stage: the CTA owns cells [i0, i0+TX) x [j0, j0+TY) of the
+// problem described by A; `nblk` is the number of tiles of that problem (the
+// last of them to finish stage 2 publishes the Courant speed).
 template <int EQ, class TC, class TS, int TX, int TY, int STAGE>
-__global__ void __launch_bounds__(TX * TY) stage2d_kernel(const Stage2DArgs<TS> A) {
+__device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, int j0,
+                                             unsigned nblk, unsigned char* smem_raw) {
   using Tr = Tr2<EQ>;
   constexpr int NV = Tr::NV, NS = Tr::NS, NP = Tr::NP, NF = Tr::NF;
   constexpr int R2X = TX + 4, R2Y = TY + 4, R2 = R2X * R2Y;
@@ -211,7 +215,6 @@ __global__ void __launch_bounds__(TX * TY) stage2d_kernel(const Stage2DArgs<TS> 
   constexpr int NT = TX * TY;
   static_assert(NT % 32 == 0, "tile must be whole warps");
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   TC* s_c0 = reinterpret_cast<TC*>(smem_raw);
   TC* s_w = s_c0 + NV * R2;
   TC* s_sl = s_w + NP * R2;
@@ -224,7 +227,6 @@ __global__ void __launch_bounds__(TX * TY) stage2d_kernel(const Stage2DArgs<TS> 
   __shared__ double s_red[NT / 32];
 
   const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int nx = A.nx, ny = A.ny;
   const size_t ncell = (size_t)A.ncell;
   Gas<TC> G;
@@ -464,7 +466,6 @@ __global__ void __launch_bounds__(TX * TY) stage2d_kernel(const Stage2DArgs<TS> 
       atomicMax(&ctl->vmax_next, (unsigned long long)__double_as_longlong(m));
       if (s_err) atomicOr(&ctl->err, s_err);
       __threadfence();
-      unsigned nblk = gridDim.x * gridDim.y;
       unsigned tk = atomicAdd(&ctl->ticket, 1u);
       if (tk == nblk - 1) {
         __threadfence();
@@ -485,6 +486,14 @@ __global__ void __launch_bounds__(TX * TY) stage2d_kernel(const Stage2DArgs<TS> 
     __syncthreads();
     if (tid == 0 && s_err) atomicOr(&A.ctl->err, s_err);
   }
+}
+
+
+template <int EQ, class TC, class TS, int TX, int TY, int STAGE>
+__global__ void __launch_bounds__(TX * TY) stage2d_kernel(const Stage2DArgs<TS> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  stage2d_tile<EQ, TC, TS, TX, TY, STAGE>(A, blockIdx.x * TX, blockIdx.y * TY,
+                                          gridDim.x * gridDim.y, smem_raw);
 }
 
 }  // namespace dgk

@@ -215,45 +215,48 @@ def euler2d_random_density(n=(256, 256), rms=0.05, ell=0.1, kmax=16, v=(1.0, 1.0
     return project_2d(f, n, gamma=gamma), delta
 
 
-def _stream_function(kmax, rng):
+def _stream_modes(kmax, rng):
     ks = [(a, b) for a in range(-kmax, kmax + 1) for b in range(0, kmax + 1)
           if (b > 0 or a > 0) and a * a + b * b <= kmax * kmax]
     ks = np.array(ks, dtype=np.float64)
     amp = rng.standard_normal(len(ks)) / (1.0 + (ks ** 2).sum(1))
     ph = rng.uniform(0, 2 * np.pi, len(ks))
+    return ks, amp, ph
 
-    def grad(X, Y):
-        # psi = sum A cos(2 pi k.x + P);  returns (d psi/dy, -d psi/dx)
-        gx = np.zeros(np.broadcast(X, Y).shape)
-        gy = np.zeros_like(gx)
-        for (a, b), A, P in zip(ks, amp, ph):
-            s = -A * np.sin(2 * np.pi * (a * X + b * Y) + P) * 2 * np.pi
-            gx += s * a
-            gy += s * b
-        return gy, -gx
 
-    return grad
+def _curl_on_grid(modes, x1, y1):
+    """(d psi/dy, -d psi/dx) of psi = sum A cos(2 pi (a x + b y) + P) on the tensor
+    grid of 1D coordinate arrays x1 [nx, 4] and y1 [ny, 4] -> [ny, nx, 4, 4]."""
+    ks, amp, ph = modes
+    gx = np.zeros((y1.shape[0], x1.shape[0], y1.shape[1], x1.shape[1]))
+    gy = np.zeros_like(gx)
+    for (a, b), A, P in zip(ks, amp, ph):
+        cx, sx = np.cos(2 * np.pi * a * x1), np.sin(2 * np.pi * a * x1)
+        cy, sy = np.cos(2 * np.pi * b * y1 + P), np.sin(2 * np.pi * b * y1 + P)
+        # sin(2 pi (a x + b y) + P) = sin(ax) cos(by + P) + cos(ax) sin(by + P)
+        s = sx[None, :, None, :] * cy[:, None, :, None] + cx[None, :, None, :] * sy[:, None, :, None]
+        s *= -2 * np.pi * A
+        gx += s * a
+        gy += s * b
+    return gy, -gx
 
 
 def mhd_random_smooth(N, kmax=4, vmax=0.3, bmax=0.3, gamma=5.0 / 3.0, rng=None):
-    """One problem of the batched workload: rho = 1, p = 1, v and B from seeded
-    random-phase stream functions (modes |k| <= kmax * 2 pi) scaled so that
-    max|v| = vmax and max|B| = bmax on the Gauss points."""
+    """One problem of the batched workload: rho = 1, p = 1, v and B the curls of
+    seeded random-phase stream functions (modes |k| <= kmax * 2 pi), scaled so that
+    max|v| = vmax and max|B| = bmax on the Gauss points; the curl of a stream
+    function is divergence free, and so is its projection on the magnetic basis."""
     rng = np.random.default_rng(1305) if rng is None else rng
-    gv = _stream_function(kmax, rng)
-    gb = _stream_function(kmax, rng)
-    X, Y, *_ = _cell_points_2d((N, N), (1.0, 1.0))
-    vx, vy = gv(X, Y)
-    bx, by = gb(X, Y)
+    mv = _stream_modes(kmax, rng)
+    mb = _stream_modes(kmax, rng)
+    h = 1.0 / N
+    x1 = (np.arange(N) + 0.5)[:, None] * h + h * GX[None, :]
+    vx, vy = _curl_on_grid(mv, x1, x1)
+    bx, by = _curl_on_grid(mb, x1, x1)
     sv = vmax / max(np.sqrt(vx * vx + vy * vy).max(), 1e-300)
     sb = bmax / max(np.sqrt(bx * bx + by * by).max(), 1e-300)
-
-    def f(Xq, Yq):
-        a, b = gv(Xq, Yq)
-        c, d = gb(Xq, Yq)
-        return 1.0, sv * a, sv * b, 1.0, sb * c, sb * d
-
-    return project_2d(f, (N, N), gamma=gamma, eq=MHD)
+    vals = (1.0, sv * vx, sv * vy, 1.0, sb * bx, sb * by)
+    return project_2d(lambda X, Y: vals, (N, N), gamma=gamma, eq=MHD)
 
 
 def batch_sizes(nprob=64, nmin=32, nmax=512, seed=1305):
