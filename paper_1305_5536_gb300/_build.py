@@ -35,9 +35,16 @@ def _deps_mtime():
     return t
 
 
+# Forward stage kernels: FP32 division and square root to within 2 ulp (the
+# single-precision path only; double precision is always IEEE-exact).
+FAST_FP32 = ["-prec-div=false", "-prec-sqrt=false"]
+FAST_FP32_SOURCES = ("dg_k2d.cu", "dg_k3d.cu", "dg_batch.cu")
+
+
 def _compile(src, extra):
     out = os.path.join(OBJ, src.replace(".cu", ".o"))
-    cmd = [_nvcc()] + ARCH + FLAGS + extra + ["-c", os.path.join(CSRC, src), "-o", out]
+    fast = FAST_FP32 if src in FAST_FP32_SOURCES else []
+    cmd = [_nvcc()] + ARCH + FLAGS + fast + extra + ["-c", os.path.join(CSRC, src), "-o", out]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))

@@ -41,6 +41,36 @@ __device__ __forceinline__ float rpow(float x, float e) { return powf(x, e); }
 __device__ __forceinline__ double rsqrtv(double x) { return sqrt(x); }
 __device__ __forceinline__ float rsqrtv(float x) { return sqrtf(x); }
 
+// Conversions between the FP64 cell averages and the arithmetic type.  For the
+// FP32 path they are done with integer operations on the IEEE-754 bit patterns,
+// because GB300 executes FP64<->FP32 conversions on its narrow FP64 pipe.
+//   to_tc(double): rebias the exponent (1023 -> 127), keep the top 23 mantissa
+//     bits rounded to nearest (ties away from zero); magnitudes below the
+//     smallest normal float become 0 (the state never holds such values).
+//   to_f64(float): exact widening; subnormal floats become 0.
+template <class T> struct Cvt;
+template <> struct Cvt<double> {
+  __device__ __forceinline__ static double to_tc(double x) { return x; }
+  __device__ __forceinline__ static double to_f64(double x) { return x; }
+};
+template <> struct Cvt<float> {
+  __device__ __forceinline__ static float to_tc(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long mag = (b & 0x7fffffffffffffffULL) + 0x10000000ULL;
+    const unsigned hi = (unsigned)(mag >> 32), lo = (unsigned)mag;
+    unsigned r = ((hi - (896u << 20)) << 3) | (lo >> 29);
+    r = hi < (897u << 20) ? 0u : r;
+    return __int_as_float((int)(r | ((unsigned)(b >> 32) & 0x80000000u)));
+  }
+  __device__ __forceinline__ static double to_f64(float f) {
+    const unsigned u = (unsigned)__float_as_int(f);
+    const unsigned m = u & 0x7fffffffu;
+    const unsigned hi = (u & 0x80000000u) | ((m >> 3) + (896u << 20));
+    const unsigned lo = m << 29;
+    return m < 0x00800000u ? 0.0 : __hiloint2double((int)hi, (int)lo);
+  }
+};
+
 // Constants of the equation of state p_gas = (gamma - 1) rho u.
 template <class T>
 struct Gas {
@@ -96,9 +126,11 @@ __device__ __forceinline__ void pressure_fn(const Gas<T>& G, T p, T rK, T pK, T 
     f = (p - pK) * q;
     df = q * (T(1) - T(0.5) * (p - pK) / (B + p));
   } else {
+    // (p/pK)^(-(g+1)/(2g)) = (p/pK)^((g-1)/(2g)) / (p/pK): one power, not two
     T pr = p / pK;
-    f = T(2) * cK * G.inv_gm1 * (rpow(pr, G.z) - T(1));
-    df = T(1) / (rK * cK) * rpow(pr, G.mzp);
+    T q = rpow(pr, G.z);
+    f = T(2) * cK * G.inv_gm1 * (q - T(1));
+    df = q / (rK * cK * pr);
   }
 }
 

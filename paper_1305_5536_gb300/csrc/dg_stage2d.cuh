@@ -247,7 +247,7 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
   for (int e = tid; e < NV * R2; e += NT) {
     int v = e / R2, r = e - v * R2;
     int ry = r / R2X, rx = r - ry * R2X;
-    s_c0[e] = (TC)__ldg(&A.in.c0[v * ncell + s_gy[ry] + s_gx[rx]]);
+    s_c0[e] = Cvt<TC>::to_tc(__ldg(&A.in.c0[v * ncell + s_gy[ry] + s_gx[rx]]));
   }
   for (int e = tid; e < NS * R1; e += NT) {
     int v = e / R1, r = e - v * R1;
@@ -267,7 +267,7 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
   }
   __syncthreads();
 
-  const TC dx = (TC)A.dx, dy = (TC)A.dy;
+  const TC dx = Cvt<TC>::to_tc(A.dx), dy = Cvt<TC>::to_tc(A.dy);
   TC hh[2] = {TC(0.5) * dx, TC(0.5) * dy};
 
   // ---- limiter on the tile and its 1-cell ring, in place
@@ -341,7 +341,7 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
   const int r2 = (ly + 2) * R2X + lx + 2, r1 = (ly + 1) * R1X + lx + 1;
   const size_t gc = (size_t)s_gy[ly + 2] + s_gx[lx + 2];
   const double dt = s_dt;
-  const TC dtc = (TC)dt;
+  const TC dtc = Cvt<TC>::to_tc(dt);
   TC c0[NV], s[NS];
 #pragma unroll
   for (int v = 0; v < NV; ++v) c0[v] = s_c0[v * R2 + r2];
@@ -395,14 +395,14 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
   if (STAGE == 1) {
     // V^1 = U^n + dt L(U^n), U^n = limited V^n
 #pragma unroll
-    for (int v = 0; v < NV; ++v) o0[v] = A.in.c0[v * ncell + gc] + dt * (double)rc0[v];
+    for (int v = 0; v < NV; ++v) o0[v] = fma(dt, Cvt<TC>::to_f64(rc0[v]), A.in.c0[v * ncell + gc]);
 #pragma unroll
     for (int k = 0; k < NS; ++k) os[k] = s[k] + dtc * rs[k];
   } else {
     // V^{n+1} = 1/2 U^n + 1/2 (U^1 + dt L(U^1)), U^n = limited V^n of this cell
     TC cn[NV], sn[NS];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) cn[v] = (TC)A.base.c0[v * ncell + gc];
+    for (int v = 0; v < NV; ++v) cn[v] = Cvt<TC>::to_tc(A.base.c0[v * ncell + gc]);
 #pragma unroll
     for (int k = 0; k < NS; ++k) sn[k] = (TC)A.base.sl[k * ncell + gc];
     if (A.limiter) {
@@ -414,14 +414,15 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
       for (int k = 0; k < 4; ++k) {
         TC c[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) c[v] = (TC)A.base.c0[v * ncell + nb[k]];
+        for (int v = 0; v < NV; ++v) c[v] = Cvt<TC>::to_tc(A.base.c0[v * ncell + nb[k]]);
         prims2d<EQ, TC>(G, c, Wn[k], err);
       }
       limit_cell2d<EQ, TC>(G, hh, W, Wn, sn);
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v)
-      o0[v] = 0.5 * A.base.c0[v * ncell + gc] + 0.5 * (A.in.c0[v * ncell + gc] + dt * (double)rc0[v]);
+      o0[v] = 0.5 * (A.base.c0[v * ncell + gc] +
+                     fma(dt, Cvt<TC>::to_f64(rc0[v]), A.in.c0[v * ncell + gc]));
 #pragma unroll
     for (int k = 0; k < NS; ++k) os[k] = TC(0.5) * sn[k] + TC(0.5) * (s[k] + dtc * rs[k]);
   }
@@ -433,12 +434,13 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
   }
 
   if (STAGE == 2) {
-    // Courant signal speed of the new state, reduced over the grid
-    double sp = 0.0;
+    // Courant signal speed of the new state, reduced over the grid (in TC; the
+    // CTA maximum is widened to FP64 for the grid-wide atomic maximum)
+    TC sp = TC(0);
     if (owner) {
       TC c[NV], W[NP];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) c[v] = (TC)o0[v];
+      for (int v = 0; v < NV; ++v) c[v] = Cvt<TC>::to_tc(o0[v]);
       prims2d<EQ, TC>(G, c, W, err);
       TC cx, cy;
       if (EQ == 0) {
@@ -448,15 +450,15 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
         cx = fast_speed(G, W[0], W[3], b2, W[4]);
         cy = fast_speed(G, W[0], W[3], b2, W[5]);
       }
-      sp = (double)((fabs(W[1]) + cx) / dx + (fabs(W[2]) + cy) / dy);
-      if (!(sp >= 0.0)) { err |= ERR_NONPHYS; sp = 0.0; }
+      sp = (fabs(W[1]) + cx) / dx + (fabs(W[2]) + cy) / dy;
+      if (!(sp >= TC(0))) { err |= ERR_NONPHYS; sp = TC(0); }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      double t = __shfl_xor_sync(0xffffffffu, sp, o);
+      TC t = __shfl_xor_sync(0xffffffffu, sp, o);
       sp = t > sp ? t : sp;
     }
-    if ((tid & 31) == 0) s_red[tid >> 5] = sp;
+    if ((tid & 31) == 0) s_red[tid >> 5] = Cvt<TC>::to_f64(sp);
     if (err) atomicOr(&s_err, err);
     __syncthreads();
     if (tid == 0) {

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs
     size_t g = (size_t)s_gz[rz] + s_gy[ry] + s_gx[rx];
     TC c[5], W[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) c[v] = (TC)__ldg(&A.in.c0[v * ncell + g]);
+    for (int v = 0; v < 5; ++v) c[v] = Cvt<TC>::to_tc(__ldg(&A.in.c0[v * ncell + g]));
     prims3d<TC>(G, c, W, err);
 #pragma unroll
     for (int q = 0; q < 5; ++q) s_w[q * R2 + r] = W[q];
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs
   }
   __syncthreads();
 
-  const TC dx = (TC)A.dx, dy = (TC)A.dy, dz = (TC)A.dz;
+  const TC dx = Cvt<TC>::to_tc(A.dx), dy = Cvt<TC>::to_tc(A.dy), dz = Cvt<TC>::to_tc(A.dz);
   const TC hh[3] = {TC(0.5) * dx, TC(0.5) * dy, TC(0.5) * dz};
   const TC oo[3] = {dx * TC(0.28867513459481288225), dy * TC(0.28867513459481288225),
                     dz * TC(0.28867513459481288225)};
@@ -342,12 +342,12 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs
   const bool owner = gi < nx && gj < ny && gk < nz;
   const size_t gc = (size_t)s_gz[lz + 2] + s_gy[ly + 2] + s_gx[lx + 2];
   const double dt = s_dt;
-  const TC dtc = (TC)dt;
+  const TC dtc = Cvt<TC>::to_tc(dt);
   double o0[5];
   TC os[15];
   if (STAGE == 1) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) o0[v] = A.in.c0[v * ncell + gc] + dt * (double)rc0[v];
+    for (int v = 0; v < 5; ++v) o0[v] = fma(dt, Cvt<TC>::to_f64(rc0[v]), A.in.c0[v * ncell + gc]);
 #pragma unroll
     for (int k = 0; k < 15; ++k) os[k] = s[k] + dtc * rs[k];
   } else {
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs
     if (A.limiter) {
       TC c[5], W[5], Wn[6][5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) c[v] = (TC)A.base.c0[v * ncell + gc];
+      for (int v = 0; v < 5; ++v) c[v] = Cvt<TC>::to_tc(A.base.c0[v * ncell + gc]);
       prims3d<TC>(G, c, W, err);
       const size_t nb[6] = {(size_t)s_gz[lz + 2] + s_gy[ly + 2] + s_gx[lx + 1],
                             (size_t)s_gz[lz + 2] + s_gy[ly + 2] + s_gx[lx + 3],
@@ -368,14 +368,15 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) c[v] = (TC)A.base.c0[v * ncell + nb[k]];
+        for (int v = 0; v < 5; ++v) c[v] = Cvt<TC>::to_tc(A.base.c0[v * ncell + nb[k]]);
         prims3d<TC>(G, c, Wn[k], err);
       }
       limit_cell3d<TC>(G, hh, W, Wn, sn);
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v)
-      o0[v] = 0.5 * A.base.c0[v * ncell + gc] + 0.5 * (A.in.c0[v * ncell + gc] + dt * (double)rc0[v]);
+      o0[v] = 0.5 * (A.base.c0[v * ncell + gc] +
+                     fma(dt, Cvt<TC>::to_f64(rc0[v]), A.in.c0[v * ncell + gc]));
 #pragma unroll
     for (int k = 0; k < 15; ++k) os[k] = TC(0.5) * sn[k] + TC(0.5) * (s[k] + dtc * rs[k]);
   }
@@ -387,22 +388,22 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs
   }
 
   if (STAGE == 2) {
-    double sp = 0.0;
+    TC sp = TC(0);
     if (owner) {
       TC c[5], W[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) c[v] = (TC)o0[v];
+      for (int v = 0; v < 5; ++v) c[v] = Cvt<TC>::to_tc(o0[v]);
       prims3d<TC>(G, c, W, err);
       TC cs = sqrt(G.g * W[4] / W[0]);
-      sp = (double)((fabs(W[1]) + cs) / dx + (fabs(W[2]) + cs) / dy + (fabs(W[3]) + cs) / dz);
-      if (!(sp >= 0.0)) { err |= ERR_NONPHYS; sp = 0.0; }
+      sp = (fabs(W[1]) + cs) / dx + (fabs(W[2]) + cs) / dy + (fabs(W[3]) + cs) / dz;
+      if (!(sp >= TC(0))) { err |= ERR_NONPHYS; sp = TC(0); }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      double t = __shfl_xor_sync(0xffffffffu, sp, o);
+      TC t = __shfl_xor_sync(0xffffffffu, sp, o);
       sp = t > sp ? t : sp;
     }
-    if ((tid & 31) == 0) s_red[tid >> 5] = sp;
+    if ((tid & 31) == 0) s_red[tid >> 5] = Cvt<TC>::to_f64(sp);
     if (err) atomicOr(&s_err, err);
     __syncthreads();
     if (tid == 0) {
