@@ -155,6 +155,18 @@ def _dist():
     return ws, rank
 
 
+def max_over_ranks(x, device="cpu"):
+    """Largest value of x over all ranks (the timed region of the slowest replica);
+    x itself when torch.distributed is not initialised."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as tdist
@@ -214,11 +226,7 @@ def run_gpu(args):
         step_ms = [a.elapsed_time(b) for a, b in evs]
         kms, kn = s.profile_read()
         s.profile(False)
-        tot = sum(step_ms)
-        if ws > 1:
-            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = max_over_ranks(sum(step_ms), "cuda")
         res = dict(ms_total=tot, ms_per_step=tot / K, kernel_ms=kms, kernel_launches=kn,
                    bytes=[s.stage_bytes(1), s.stage_bytes(2)], wall_s=t_wall,
                    clocks=sampler.summary() if sampler else None)
