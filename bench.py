@@ -38,6 +38,9 @@ WORKLOADS = {
         "limiter, CFL 0.3")),
     "kh3d_256": dict(eq="euler", dim=3, n=(256, 256, 256), desc=(
         "3D Euler Kelvin-Helmholtz shear layer 256^3, exact Riemann, limiter, CFL 0.3")),
+    "kh3d_128": dict(eq="euler", dim=3, n=(128, 128, 128), desc=(
+        "3D Euler Kelvin-Helmholtz shear layer 128^3 (profiling size), exact Riemann, limiter, "
+        "CFL 0.3")),
     "mhd_batch64": dict(eq="mhd", dim=2, n=None, desc=(
         "64 independent 2D ideal-MHD problems, N log-uniform in [32, 512] (seeded), "
         "random-phase smooth v and div-free B, one persistent launch per step, CFL 0.3")),

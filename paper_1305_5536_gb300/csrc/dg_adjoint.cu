@@ -495,6 +495,7 @@ Stage2DArgs<TS> stage_args(const AdjointCall& c, const Work& w, StateBuf<TS> in,
   a.nx = c.nx; a.ny = c.ny; a.ncell = (long)c.nx * c.ny;
   a.dx = c.dx; a.dy = c.dy;
   a.gamma = c.gamma; a.cfl = 0.3; a.dt_override = dt; a.limiter = c.limiter;
+  a.gas.set(c.gamma);
   a.in = in; a.base = base; a.out = out;
   a.ctl = w.ctl;
   return a;

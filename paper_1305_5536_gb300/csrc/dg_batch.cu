@@ -68,6 +68,7 @@ __device__ __forceinline__ Stage2DArgs<TS> problem_args(const BatchArgs<TS>& B, 
   a.dx = p.dx;
   a.dy = p.dy;
   a.gamma = B.gamma;
+  a.gas = B.gas;
   a.cfl = B.cfl;
   a.dt_override = B.dt_override;
   a.limiter = B.limiter;

@@ -26,6 +26,7 @@ struct BatchArgs {
   int nprob;
   int ntiles;
   double gamma, cfl, dt_override;
+  GasPair gas;
   int limiter;
   double* c0[3];
   TS* sl[3];

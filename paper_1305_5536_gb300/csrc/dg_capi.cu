@@ -201,6 +201,7 @@ cudaError_t launch_batch_step_t(dg_ctx* c, int a, int b, double dtov) {
   B.nprob = (int)c->probs.size();
   B.ntiles = c->btiles[v];
   B.gamma = c->gamma;
+  B.gas.set(c->gamma);
   B.cfl = c->cfl;
   B.dt_override = dtov;
   B.limiter = c->limiter;
@@ -225,6 +226,7 @@ cudaError_t launch_stage_t(dg_ctx* c, int stage, int in, int base, int out, doub
       a.nx = p.nx; a.ny = p.ny; a.ncell = p.ncell;
       a.dx = p.dx; a.dy = p.dy;
       a.gamma = c->gamma; a.cfl = c->cfl; a.dt_override = dtov; a.limiter = c->limiter;
+      a.gas.set(c->gamma);
       a.in = sbuf<TS>(c, in, p);
       a.base = sbuf<TS>(c, base, p);
       a.out = sbuf<TS>(c, out, p);
@@ -237,6 +239,7 @@ cudaError_t launch_stage_t(dg_ctx* c, int stage, int in, int base, int out, doub
       a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.ncell = p.ncell;
       a.dx = p.dx; a.dy = p.dy; a.dz = p.dz;
       a.gamma = c->gamma; a.cfl = c->cfl; a.dt_override = dtov; a.limiter = c->limiter;
+      a.gas.set(c->gamma);
       a.in = sbuf<TS>(c, in, p);
       a.base = sbuf<TS>(c, base, p);
       a.out = sbuf<TS>(c, out, p);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dg_physics.cuh"
+
 namespace dgk {
 
 // Per-problem control block in device memory.  The Courant time step of the
@@ -30,6 +32,20 @@ struct StateBuf {
   TS* sl;
 };
 
+// Constants of the equation of state in both arithmetic types, derived once on
+// the host (deriving them per thread would put double divisions on the FP64 pipe).
+struct GasPair {
+  Gas<double> d;
+  Gas<float> f;
+  __host__ void set(double gamma) {
+    d.set(gamma);
+    f.set(gamma);
+  }
+};
+template <class T> __device__ __forceinline__ const Gas<T>& gas_of(const GasPair& g);
+template <> __device__ __forceinline__ const Gas<double>& gas_of<double>(const GasPair& g) { return g.d; }
+template <> __device__ __forceinline__ const Gas<float>& gas_of<float>(const GasPair& g) { return g.f; }
+
 // Arguments of one stage launch on one periodic 2D grid.
 template <class TS>
 struct Stage2DArgs {
@@ -37,6 +53,7 @@ struct Stage2DArgs {
   long ncell;
   double dx, dy;
   double gamma, cfl, dt_override;
+  GasPair gas;
   int limiter;
   StateBuf<TS> in;    // stage input (V^n in stage 1, V^1 in stage 2)
   StateBuf<TS> base;  // V^n (stage 2 only)
@@ -51,6 +68,7 @@ struct Stage3DArgs {
   long ncell;
   double dx, dy, dz;
   double gamma, cfl, dt_override;
+  GasPair gas;
   int limiter;
   StateBuf<TS> in;
   StateBuf<TS> base;

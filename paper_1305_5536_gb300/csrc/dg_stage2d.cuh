@@ -229,8 +229,7 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
   const int tid = threadIdx.x;
   const int nx = A.nx, ny = A.ny;
   const size_t ncell = (size_t)A.ncell;
-  Gas<TC> G;
-  G.set(A.gamma);
+  const Gas<TC> G = gas_of<TC>(A.gas);
   unsigned err = 0;
 
   if (tid == 0) {
@@ -326,10 +325,10 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
     face_flux2d<EQ, TC>(G, xf ? 0 : 1, cl, cr, F, err);
     if (xf) {
 #pragma unroll
-      for (int q = 0; q < NF; ++q) s_fx[(q * 2 + g) * NFX + f] = F[q];
+      for (int q = 0; q < NF; ++q) s_fx[(q * NFX + f) * 2 + g] = F[q];
     } else {
 #pragma unroll
-      for (int q = 0; q < NF; ++q) s_fy[(q * 2 + g) * NFY + f] = F[q];
+      for (int q = 0; q < NF; ++q) s_fy[(q * NFY + f) * 2 + g] = F[q];
     }
   }
   __syncthreads();
@@ -364,11 +363,11 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
   TC Sxm[NF], Sxp[NF], Dxm[NF], Dxp[NF], Sym[NF], Syp[NF], Dym[NF], Dyp[NF];
 #pragma unroll
   for (int q = 0; q < NF; ++q) {
-    TC a0 = s_fx[(q * 2) * NFX + fxm], a1 = s_fx[(q * 2 + 1) * NFX + fxm];
-    TC b0 = s_fx[(q * 2) * NFX + fxm + 1], b1 = s_fx[(q * 2 + 1) * NFX + fxm + 1];
+    TC a0 = s_fx[(q * NFX + fxm) * 2], a1 = s_fx[(q * NFX + fxm) * 2 + 1];
+    TC b0 = s_fx[(q * NFX + fxm + 1) * 2], b1 = s_fx[(q * NFX + fxm + 1) * 2 + 1];
     Sxm[q] = a0 + a1; Dxm[q] = a1 - a0; Sxp[q] = b0 + b1; Dxp[q] = b1 - b0;
-    a0 = s_fy[(q * 2) * NFY + fym]; a1 = s_fy[(q * 2 + 1) * NFY + fym];
-    b0 = s_fy[(q * 2) * NFY + fym + TX]; b1 = s_fy[(q * 2 + 1) * NFY + fym + TX];
+    a0 = s_fy[(q * NFY + fym) * 2]; a1 = s_fy[(q * NFY + fym) * 2 + 1];
+    b0 = s_fy[(q * NFY + fym + TX) * 2]; b1 = s_fy[(q * NFY + fym + TX) * 2 + 1];
     Sym[q] = a0 + a1; Dym[q] = a1 - a0; Syp[q] = b0 + b1; Dyp[q] = b1 - b0;
   }
   const TC inv2dx = TC(0.5) / dx, inv2dy = TC(0.5) / dy;

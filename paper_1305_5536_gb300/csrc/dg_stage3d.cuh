@@ -124,25 +124,54 @@ __device__ __forceinline__ void phys_flux3d(const Gas<TC>& G, const TC* c, int d
   F[4] = (c[4] + p) * vd;
 }
 
-// Exact-solver flux through a face along axis d between conserved cl, cr; lab
-// frame (rho, mx, my, mz, E).
+// Exact-solver flux through a face along axis d (0, 1, 2; uniform across the
+// CTA) between conserved cl, cr; lab frame (rho, mx, my, mz, E).  Normal and
+// transverse components are picked with selects, so one inlined copy of the
+// solver serves all three orientations.
 template <class TC>
 __device__ __forceinline__ void face_flux3d(const Gas<TC>& G, int d, const TC* cl, const TC* cr,
                                             TC* F, unsigned& err) {
   TC il = TC(1) / cl[0], ir = TC(1) / cr[0];
-  TC vl[3] = {cl[1] * il, cl[2] * il, cl[3] * il};
-  TC vr[3] = {cr[1] * ir, cr[2] * ir, cr[3] * ir};
-  TC pl = G.gm1 * (cl[4] - TC(0.5) * (cl[1] * vl[0] + cl[2] * vl[1] + cl[3] * vl[2]));
-  TC pr = G.gm1 * (cr[4] - TC(0.5) * (cr[1] * vr[0] + cr[2] * vr[1] + cr[3] * vr[2]));
-  const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-  TC tl[2] = {vl[t1], vl[t2]}, tr[2] = {vr[t1], vr[t2]};
+  TC lx = cl[1] * il, ly = cl[2] * il, lz = cl[3] * il;
+  TC rx = cr[1] * ir, ry = cr[2] * ir, rz = cr[3] * ir;
+  TC pl = G.gm1 * (cl[4] - TC(0.5) * (cl[1] * lx + cl[2] * ly + cl[3] * lz));
+  TC pr = G.gm1 * (cr[4] - TC(0.5) * (cr[1] * rx + cr[2] * ry + cr[3] * rz));
+  // normal n, transverse t1 (x unless d == 0), t2 (z unless d == 2)
+  const TC nl = d == 0 ? lx : (d == 1 ? ly : lz), nr = d == 0 ? rx : (d == 1 ? ry : rz);
+  TC tl[2] = {d == 0 ? ly : lx, d == 2 ? ly : lz};
+  TC tr[2] = {d == 0 ? ry : rx, d == 2 ? ry : rz};
   TC Ff[5];
-  exact_flux<TC, 2>(G, cl[0], vl[d], pl, tl, cr[0], vr[d], pr, tr, Ff, err);
+  exact_flux<TC, 2>(G, cl[0], nl, pl, tl, cr[0], nr, pr, tr, Ff, err);
   F[0] = Ff[0];
-  F[1 + d] = Ff[1];
-  F[1 + t1] = Ff[2];
-  F[1 + t2] = Ff[3];
+  F[1] = d == 0 ? Ff[1] : Ff[2];
+  F[2] = d == 1 ? Ff[1] : (d == 0 ? Ff[2] : Ff[3]);
+  F[3] = d == 2 ? Ff[1] : Ff[3];
   F[4] = Ff[4];
+}
+
+// Add the two faces of orientation D of a cell to its right-hand side; s_f holds
+// [var][face][gauss point] with the 2x2 points in the order (a, b) = (--, -+, +-, ++)
+// of the transverse axes (e1, e2).
+template <int D, class TC>
+__device__ __forceinline__ void gather3d(const TC* s_f, int FMAX, int fm, int fp, const TC* hd,
+                                         TC* rc0, TC* rs) {
+  constexpr int E1 = D == 0 ? 1 : 0, E2 = D == 2 ? 1 : 2;
+  const TC c0f = TC(0.25) / hd[D];
+  const TC csf = TC(1.5) / (hd[D] * hd[D]);
+  const TC ce1 = TC(0.86602540378443864676) / (hd[E1] * hd[D]);
+  const TC ce2 = TC(0.86602540378443864676) / (hd[E2] * hd[D]);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const TC* m = s_f + (v * FMAX + fm) * 4;
+    const TC* p = s_f + (v * FMAX + fp) * 4;
+    TC Sm = (m[0] + m[1]) + (m[2] + m[3]), Sp = (p[0] + p[1]) + (p[2] + p[3]);
+    TC Dm1 = (m[2] + m[3]) - (m[0] + m[1]), Dp1 = (p[2] + p[3]) - (p[0] + p[1]);
+    TC Dm2 = (m[1] + m[3]) - (m[0] + m[2]), Dp2 = (p[1] + p[3]) - (p[0] + p[2]);
+    rc0[v] -= (Sp - Sm) * c0f;
+    rs[3 * v + D] -= csf * (Sp + Sm);
+    rs[3 * v + E1] -= ce1 * (Dp1 - Dm1);
+    rs[3 * v + E2] -= ce2 * (Dp2 - Dm2);
+  }
 }
 
 template <class TC, class TS, int TX, int TY, int TZ, int STAGE>
@@ -169,8 +198,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * TZ;
   const int nx = A.nx, ny = A.ny, nz = A.nz;
   const size_t ncell = (size_t)A.ncell;
-  Gas<TC> G;
-  G.set(A.gamma);
+  const Gas<TC> G = gas_of<TC>(A.gas);
   unsigned err = 0;
   if (tid == 0) {
     s_err = 0;
@@ -277,13 +305,15 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs
       for (int d = 0; d < 3; ++d) rs[3 * v + d] = TC(1.5) / (hd[d] * hd[d]) * sF[d][v];
   }
 
-  // ---- faces, one orientation at a time
+  // ---- faces, one orientation at a time (rolled loop: one copy of the solver)
   const TC hd[3] = {dx, dy, dz};
-#pragma unroll
+#pragma unroll 1
   for (int d = 0; d < 3; ++d) {
     const int FX = TX + (d == 0), FY = TY + (d == 1), FZ = TZ + (d == 2);
     const int NFACE = FX * FY * FZ;
-    const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+    const int step = d == 0 ? 1 : (d == 1 ? R1X : R1X * R1Y);
+    const TC hn = d == 0 ? hh[0] : (d == 1 ? hh[1] : hh[2]);
+    const TC o1 = d == 0 ? oo[1] : oo[0], o2 = d == 2 ? oo[1] : oo[2];
     for (int e = tid; e < 4 * NFACE; e += NT) {
       const int f = e >> 2, g = e & 3;
       const int fz = f / (FX * FY), fr = f - fz * (FX * FY);
@@ -292,47 +322,31 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs
       // i.e. halo-1 coordinates (fx+1, fy+1, fz+1); the - side is one step back
       // along d
       const int r1r = ((fz + 1) * R1Y + (fy + 1)) * R1X + (fx + 1);
-      const int step = d == 0 ? 1 : (d == 1 ? R1X : R1X * R1Y);
       const int r1l = r1r - step;
-      TC pl[3], pr[3];
-      pl[d] = hh[d];
-      pr[d] = -hh[d];
-      const TC a = (g & 2) ? oo[e1] : -oo[e1], b = (g & 1) ? oo[e2] : -oo[e2];
-      pl[e1] = pr[e1] = a;
-      pl[e2] = pr[e2] = b;
+      const TC a = (g & 2) ? o1 : -o1, b = (g & 1) ? o2 : -o2;
+      // local coordinates of the Gauss point in the - cell (normal +hn) and the
+      // + cell (normal -hn)
+      const TC xl = d == 0 ? hn : a, xr = d == 0 ? -hn : a;
+      const TC yl = d == 1 ? hn : (d == 0 ? a : b), yr = d == 1 ? -hn : (d == 0 ? a : b);
+      const TC zl = d == 2 ? hn : b, zr = d == 2 ? -hn : b;
       TC cl0[5], cr0[5], sl[15], sr[15], cl[5], cr[5], F[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) { cl0[v] = s_c0[v * R1 + r1l]; cr0[v] = s_c0[v * R1 + r1r]; }
 #pragma unroll
       for (int k = 0; k < 15; ++k) { sl[k] = s_sl[k * R1 + r1l]; sr[k] = s_sl[k * R1 + r1r]; }
-      eval3d<TC>(cl0, sl, pl[0], pl[1], pl[2], cl);
-      eval3d<TC>(cr0, sr, pr[0], pr[1], pr[2], cr);
+      eval3d<TC>(cl0, sl, xl, yl, zl, cl);
+      eval3d<TC>(cr0, sr, xr, yr, zr, cr);
       face_flux3d<TC>(G, d, cl, cr, F, err);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) s_f[(v * 4 + g) * FMAX + f] = F[v];
+      for (int v = 0; v < 5; ++v) s_f[(v * FMAX + f) * 4 + g] = F[v];
     }
     __syncthreads();
     {
       const int fm = (lz * FY + ly) * FX + lx;
       const int fp = fm + (d == 0 ? 1 : (d == 1 ? FX : FX * FY));
-      const TC c0f = TC(0.25) / hd[d];
-      const TC csf = TC(1.5) / (hd[d] * hd[d]);
-      const TC ce1 = TC(0.86602540378443864676) / (hd[e1] * hd[d]);
-      const TC ce2 = TC(0.86602540378443864676) / (hd[e2] * hd[d]);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        TC m0 = s_f[(v * 4 + 0) * FMAX + fm], m1 = s_f[(v * 4 + 1) * FMAX + fm];
-        TC m2 = s_f[(v * 4 + 2) * FMAX + fm], m3 = s_f[(v * 4 + 3) * FMAX + fm];
-        TC p0 = s_f[(v * 4 + 0) * FMAX + fp], p1 = s_f[(v * 4 + 1) * FMAX + fp];
-        TC p2 = s_f[(v * 4 + 2) * FMAX + fp], p3 = s_f[(v * 4 + 3) * FMAX + fp];
-        TC Sm = (m0 + m1) + (m2 + m3), Sp = (p0 + p1) + (p2 + p3);
-        TC Dm1 = (m2 + m3) - (m0 + m1), Dp1 = (p2 + p3) - (p0 + p1);
-        TC Dm2 = (m1 + m3) - (m0 + m2), Dp2 = (p1 + p3) - (p0 + p2);
-        rc0[v] -= (Sp - Sm) * c0f;
-        rs[3 * v + d] -= csf * (Sp + Sm);
-        rs[3 * v + e1] -= ce1 * (Dp1 - Dm1);
-        rs[3 * v + e2] -= ce2 * (Dp2 - Dm2);
-      }
+      if (d == 0) gather3d<0, TC>(s_f, FMAX, fm, fp, hd, rc0, rs);
+      else if (d == 1) gather3d<1, TC>(s_f, FMAX, fm, fp, hd, rc0, rs);
+      else gather3d<2, TC>(s_f, FMAX, fm, fp, hd, rc0, rs);
     }
     __syncthreads();
   }
