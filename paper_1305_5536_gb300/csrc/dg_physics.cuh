@@ -36,8 +36,11 @@ template <> struct Prec<float> {
   static constexpr float hlld_degenerate = 1e-8f;
 };
 
+// Powers in the exact solver (positive bases only).  FP64: the accurate pow.
+// FP32: the __powf intrinsic (exp2 of e * log2 x on the special-function unit),
+// a few ulp for the exponents used here, ~10x fewer instructions than powf.
 __device__ __forceinline__ double rpow(double x, double e) { return pow(x, e); }
-__device__ __forceinline__ float rpow(float x, float e) { return powf(x, e); }
+__device__ __forceinline__ float rpow(float x, float e) { return __powf(x, e); }
 __device__ __forceinline__ double rsqrtv(double x) { return sqrt(x); }
 __device__ __forceinline__ float rsqrtv(float x) { return sqrtf(x); }
 
