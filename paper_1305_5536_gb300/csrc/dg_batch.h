@@ -36,8 +36,6 @@ struct BatchArgs {
   int barrier_extra;      // expected arrivals beyond the grid (0; 1 in a timeout test)
 };
 
-enum : unsigned { ERR_TIMEOUT = 8u };
-
 cudaError_t launch_batch2d(int eq, int variant, const BatchArgs<double>& B, cudaStream_t st,
                            int* grid);
 cudaError_t launch_batch2d(int eq, int variant, const BatchArgs<float>& B, cudaStream_t st,

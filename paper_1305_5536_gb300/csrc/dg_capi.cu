@@ -71,7 +71,7 @@ struct dg_ctx {
   AdjointStore adj;
   // batched 2D problems: one persistent launch per step over a tile work list
   bool batch2d = false;
-  BatchProb* btab[3] = {nullptr, nullptr, nullptr};  // per tile variant
+  BatchProb* btab[3] = {nullptr, nullptr, nullptr};  // per tile variant of the batch kernel
   int btiles[3] = {0, 0, 0};
   unsigned* bar = nullptr;
   long long spin_limit = 1LL << 24;
@@ -193,9 +193,13 @@ void free_graphs(dg_ctx* c) {
 // ---------------------------------------------------------------------------
 // stage launches
 // ---------------------------------------------------------------------------
+// Tile shapes compiled for the batched kernel (one work list each).
+constexpr int kBatchVariants = 3;
+
 template <class TS>
 cudaError_t launch_batch_step_t(dg_ctx* c, int a, int b, double dtov) {
   const int v = c->variant < 0 ? 0 : c->variant;
+  if (v >= kBatchVariants) return cudaErrorInvalidValue;  // no work list for it
   BatchArgs<TS> B;
   B.probs = c->btab[v];
   B.nprob = (int)c->probs.size();
@@ -412,6 +416,12 @@ void tune_save() {
 
 dg_status autotune(dg_ctx* c) {
   if (c->variant >= 0) return DG_OK;
+  // an explicit choice (DG_TILE_VARIANT) wins over the tuning cache
+  const char* env = getenv("DG_TILE_VARIANT");
+  if (env) {
+    c->variant = atoi(env);
+    return DG_OK;
+  }
   tune_load();
   std::string key = tune_key(c);
   auto it = g_tune.find(key);
@@ -419,12 +429,8 @@ dg_status autotune(dg_ctx* c) {
     c->variant = it->second;
     return DG_OK;
   }
-  const char* env = getenv("DG_TILE_VARIANT");
-  if (env) {
-    c->variant = atoi(env);
-    return DG_OK;
-  }
-  int nvar = c->dim == 2 ? stage2d_variants(c->eq, c->fp32) : stage3d_variants(c->fp32);
+  int nvar = c->batch2d ? kBatchVariants
+                        : (c->dim == 2 ? stage2d_variants(c->eq, c->fp32) : stage3d_variants(c->fp32));
   if (nvar <= 1) {
     c->variant = 0;
     return DG_OK;
@@ -442,16 +448,22 @@ dg_status autotune(dg_ctx* c) {
   for (int v = 0; v < nvar; ++v) {
     c->variant = v;
     float tot = 0.0f;
-    for (int rep = 0; rep < 4; ++rep) {
+    bool ok = true;
+    for (int rep = 0; rep < 4 && ok; ++rep) {
       CK(c, cudaEventRecord(e0, c->stream));
-      CK(c, launch_step(c, c->cur, c->nxt, dt));
+      if (launch_step(c, c->cur, c->nxt, dt) != cudaSuccess) {
+        // this shape does not apply to the grid (e.g. TMA rows not 16-byte aligned)
+        cudaGetLastError();
+        ok = false;
+        break;
+      }
       CK(c, cudaEventRecord(e1, c->stream));
       CK(c, cudaEventSynchronize(e1));
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, e0, e1);
       if (rep > 0) tot += ms;
     }
-    if (tot < best) {
+    if (ok && tot < best) {
       best = tot;
       bestv = v;
     }

@@ -22,6 +22,7 @@ enum : unsigned {
   ERR_NONPHYS = 1u,   // rho <= 0 or p <= 0 at an evaluated state
   ERR_VACUUM = 2u,    // the exact solver met a vacuum-generating pair
   ERR_NEWTON = 4u,    // Newton iteration for p* did not converge
+  ERR_TIMEOUT = 8u,   // a bounded device wait (grid barrier, TMA completion) ran out
 };
 
 template <class T> struct Prec;

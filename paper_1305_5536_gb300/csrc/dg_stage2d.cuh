@@ -41,13 +41,56 @@ template <> struct Tr2<1> {  // planar MHD: (rho, mx, my, E, b1, b2) + (.., a1, 
   static constexpr int NV = 6, NS = 11, NP = 6, NF = 5;
 };
 
+// Shared-memory working set of one tile (element counts of the arithmetic type
+// TC): averages [NV][R2], derivative coefficients [NS][R1], and one region that
+// first holds the centroid primitives [NP][R2] and, once the limiter is done with
+// them, the face fluxes [NF][(TX+1)TY][2] and [NF][TX(TY+1)][2].
+template <int EQ, int TX, int TY>
+struct Tile2D {
+  using Tr = Tr2<EQ>;
+  static constexpr int NV = Tr::NV, NS = Tr::NS, NP = Tr::NP, NF = Tr::NF;
+  static constexpr int R2X = TX + 4, R2Y = TY + 4, R2 = R2X * R2Y;
+  static constexpr int R1X = TX + 2, R1Y = TY + 2, R1 = R1X * R1Y;
+  static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
+  static constexpr int NT = TX * TY;
+  static constexpr int WSZ = NP * R2 > NF * 2 * (NFX + NFY) ? NP * R2 : NF * 2 * (NFX + NFY);
+  static constexpr int ELEMS = NV * R2 + NS * R1 + WSZ;
+};
+
 template <int EQ, int TX, int TY, class TC>
 __host__ __device__ constexpr size_t stage2d_smem_bytes() {
-  using Tr = Tr2<EQ>;
-  return (size_t(Tr::NV + Tr::NP) * (TX + 4) * (TY + 4) + size_t(Tr::NS) * (TX + 2) * (TY + 2) +
-          size_t(Tr::NF) * 2 * ((TX + 1) * TY + TX * (TY + 1))) * sizeof(TC) +
-         sizeof(int) * ((TX + 4) + (TY + 4));
+  using T = Tile2D<EQ, TX, TY>;
+  return size_t(T::ELEMS) * sizeof(TC) + sizeof(int) * (T::R2X + T::R2Y);
 }
+
+template <class TC>
+struct TileMem {
+  TC* c0;
+  TC* sl;
+  TC* w;  // primitives, then face fluxes
+  int* gx;
+  int* gy;
+};
+
+template <int EQ, int TX, int TY, class TC>
+__device__ __forceinline__ TileMem<TC> tile_mem(unsigned char* base) {
+  using T = Tile2D<EQ, TX, TY>;
+  TileMem<TC> m;
+  m.c0 = reinterpret_cast<TC*>(base);
+  m.sl = m.c0 + T::NV * T::R2;
+  m.w = m.sl + T::NS * T::R1;
+  m.gx = reinterpret_cast<int*>(m.w + T::WSZ);
+  m.gy = m.gx + T::R2X;
+  return m;
+}
+
+// Per-tile scalars shared by the CTA.
+template <int NT>
+struct TileScalars {
+  double dt;
+  unsigned err;
+  double red[NT / 32];
+};
 
 // Centroid primitives (rho, vx, vy, p[, Bx, By]) from averages.
 template <int EQ, class TC>
@@ -201,12 +244,48 @@ __device__ __forceinline__ void face_flux2d(const Gas<TC>& G, int dir, const TC*
   else { F[1] = Ff[2]; F[2] = Ff[1]; }
 }
 
-// One tile of one stage: the CTA owns cells [i0, i0+TX) x [j0, j0+TY) of the
-// problem described by A; `nblk` is the number of tiles of that problem (the
-// last of them to finish stage 2 publishes the Courant speed).
+// Start of a tile: the time step, the error word, and the wrapped global row and
+// column offsets of the halo-2 region.  The caller synchronises afterwards.
+template <int EQ, class TC, class TS, int TX, int TY>
+__device__ __forceinline__ void stage2d_setup(const Stage2DArgs<TS>& A, int i0, int j0,
+                                              const TileMem<TC>& M, TileScalars<TX * TY>& S) {
+  using T = Tile2D<EQ, TX, TY>;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    S.err = 0;
+    double dt = A.dt_override > 0.0 ? A.dt_override : A.cfl / A.ctl->vmax_cur;
+    if (!(dt > 0.0) || !(dt < 1e300)) S.err |= ERR_NONPHYS;
+    S.dt = dt;
+  }
+  if (tid < T::R2X) M.gx[tid] = wrap_index(i0 - 2 + tid, A.nx);
+  else if (tid < T::R2X + T::R2Y) M.gy[tid - T::R2X] = wrap_index(j0 - 2 + (tid - T::R2X), A.ny) * A.nx;
+}
+
+// Stage the tile from global memory element by element (periodic wrap): averages
+// with halo 2, derivative coefficients with halo 1.  The caller synchronises.
+template <int EQ, class TC, class TS, int TX, int TY>
+__device__ __forceinline__ void stage2d_load(const Stage2DArgs<TS>& A, const TileMem<TC>& M) {
+  using T = Tile2D<EQ, TX, TY>;
+  const size_t ncell = (size_t)A.ncell;
+  for (int e = threadIdx.x; e < T::NV * T::R2; e += T::NT) {
+    int v = e / T::R2, r = e - v * T::R2;
+    int ry = r / T::R2X, rx = r - ry * T::R2X;
+    M.c0[e] = Cvt<TC>::to_tc(__ldg(&A.in.c0[v * ncell + M.gy[ry] + M.gx[rx]]));
+  }
+  for (int e = threadIdx.x; e < T::NS * T::R1; e += T::NT) {
+    int v = e / T::R1, r = e - v * T::R1;
+    int ry = r / T::R1X, rx = r - ry * T::R1X;
+    M.sl[e] = (TC)__ldg(&A.in.sl[v * ncell + M.gy[ry + 1] + M.gx[rx + 1]]);
+  }
+}
+
+// The rest of a tile once it is staged: primitives, limiter, faces, per-cell
+// right-hand side and Runge-Kutta combination; `nblk` is the number of tiles of
+// the problem (the last of them to finish stage 2 publishes the Courant speed).
 template <int EQ, class TC, class TS, int TX, int TY, int STAGE>
-__device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, int j0,
-                                             unsigned nblk, unsigned char* smem_raw) {
+__device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0, int j0,
+                                                unsigned nblk, const TileMem<TC>& M,
+                                                TileScalars<TX * TY>& S) {
   using Tr = Tr2<EQ>;
   constexpr int NV = Tr::NV, NS = Tr::NS, NP = Tr::NP, NF = Tr::NF;
   constexpr int R2X = TX + 4, R2Y = TY + 4, R2 = R2X * R2Y;
@@ -214,46 +293,21 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
   constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
   constexpr int NT = TX * TY;
   static_assert(NT % 32 == 0, "tile must be whole warps");
-
-  TC* s_c0 = reinterpret_cast<TC*>(smem_raw);
-  TC* s_w = s_c0 + NV * R2;
-  TC* s_sl = s_w + NP * R2;
-  TC* s_fx = s_sl + NS * R1;
-  TC* s_fy = s_fx + NF * 2 * NFX;
-  int* s_gx = reinterpret_cast<int*>(s_fy + NF * 2 * NFY);
-  int* s_gy = s_gx + R2X;
-  __shared__ double s_dt;
-  __shared__ unsigned s_err;
-  __shared__ double s_red[NT / 32];
+  (void)R2Y;
+  (void)R1Y;
+  TC* s_c0 = M.c0;
+  TC* s_w = M.w;
+  TC* s_sl = M.sl;
+  TC* s_fx = M.w;
+  TC* s_fy = M.w + NF * 2 * NFX;
+  const int* s_gx = M.gx;
+  const int* s_gy = M.gy;
 
   const int tid = threadIdx.x;
   const int nx = A.nx, ny = A.ny;
   const size_t ncell = (size_t)A.ncell;
   const Gas<TC> G = gas_of<TC>(A.gas);
   unsigned err = 0;
-
-  if (tid == 0) {
-    s_err = 0;
-    double dt = A.dt_override > 0.0 ? A.dt_override : A.cfl / A.ctl->vmax_cur;
-    if (!(dt > 0.0) || !(dt < 1e300)) err |= ERR_NONPHYS;
-    s_dt = dt;
-  }
-  if (tid < R2X) s_gx[tid] = wrap_index(i0 - 2 + tid, nx);
-  else if (tid < R2X + R2Y) s_gy[tid - R2X] = wrap_index(j0 - 2 + (tid - R2X), ny) * nx;
-  __syncthreads();
-
-  // ---- stage the tile: averages with halo 2, derivatives with halo 1
-  for (int e = tid; e < NV * R2; e += NT) {
-    int v = e / R2, r = e - v * R2;
-    int ry = r / R2X, rx = r - ry * R2X;
-    s_c0[e] = Cvt<TC>::to_tc(__ldg(&A.in.c0[v * ncell + s_gy[ry] + s_gx[rx]]));
-  }
-  for (int e = tid; e < NS * R1; e += NT) {
-    int v = e / R1, r = e - v * R1;
-    int ry = r / R1X, rx = r - ry * R1X;
-    s_sl[e] = (TC)__ldg(&A.in.sl[v * ncell + s_gy[ry + 1] + s_gx[rx + 1]]);
-  }
-  __syncthreads();
 
   // ---- centroid primitives of every staged cell
   for (int r = tid; r < R2; r += NT) {
@@ -289,8 +343,8 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
 #pragma unroll
       for (int k = 0; k < NS; ++k) s_sl[k * R1 + r1] = s[k];
     }
-    __syncthreads();
   }
+  __syncthreads();  // the primitives are dead from here: their space takes the fluxes
 
   // ---- faces: Riemann fluxes at the Gauss points, each face once
   const TC ox = dx * TC(0.28867513459481288225), oy = dy * TC(0.28867513459481288225);
@@ -339,7 +393,7 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
   const bool owner = gi < nx && gj < ny;
   const int r2 = (ly + 2) * R2X + lx + 2, r1 = (ly + 1) * R1X + lx + 1;
   const size_t gc = (size_t)s_gy[ly + 2] + s_gx[lx + 2];
-  const double dt = s_dt;
+  const double dt = S.dt;
   const TC dtc = Cvt<TC>::to_tc(dt);
   TC c0[NV], s[NS];
 #pragma unroll
@@ -457,15 +511,15 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
       TC t = __shfl_xor_sync(0xffffffffu, sp, o);
       sp = t > sp ? t : sp;
     }
-    if ((tid & 31) == 0) s_red[tid >> 5] = Cvt<TC>::to_f64(sp);
-    if (err) atomicOr(&s_err, err);
+    if ((tid & 31) == 0) S.red[tid >> 5] = Cvt<TC>::to_f64(sp);
+    if (err) atomicOr(&S.err, err);
     __syncthreads();
     if (tid == 0) {
       double m = 0.0;
-      for (int w = 0; w < NT / 32; ++w) m = s_red[w] > m ? s_red[w] : m;
+      for (int w = 0; w < NT / 32; ++w) m = S.red[w] > m ? S.red[w] : m;
       Ctl* ctl = A.ctl;
       atomicMax(&ctl->vmax_next, (unsigned long long)__double_as_longlong(m));
-      if (s_err) atomicOr(&ctl->err, s_err);
+      if (S.err) atomicOr(&ctl->err, S.err);
       __threadfence();
       unsigned tk = atomicAdd(&ctl->ticket, 1u);
       if (tk == nblk - 1) {
@@ -483,12 +537,27 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
       }
     }
   } else {
-    if (err) atomicOr(&s_err, err);
+    if (err) atomicOr(&S.err, err);
     __syncthreads();
-    if (tid == 0 && s_err) atomicOr(&A.ctl->err, s_err);
+    if (tid == 0 && S.err) atomicOr(&A.ctl->err, S.err);
   }
 }
 
+
+
+// One tile of one stage (classic staging): the CTA owns cells [i0, i0+TX) x
+// [j0, j0+TY) of the problem described by A.
+template <int EQ, class TC, class TS, int TX, int TY, int STAGE>
+__device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, int j0,
+                                             unsigned nblk, unsigned char* smem_raw) {
+  __shared__ TileScalars<TX * TY> S;
+  const TileMem<TC> M = tile_mem<EQ, TX, TY, TC>(smem_raw);
+  stage2d_setup<EQ, TC, TS, TX, TY>(A, i0, j0, M, S);
+  __syncthreads();
+  stage2d_load<EQ, TC, TS, TX, TY>(A, M);
+  __syncthreads();
+  stage2d_compute<EQ, TC, TS, TX, TY, STAGE>(A, i0, j0, nblk, M, S);
+}
 
 template <int EQ, class TC, class TS, int TX, int TY, int STAGE>
 __global__ void __launch_bounds__(TX * TY) stage2d_kernel(const Stage2DArgs<TS> A) {
