@@ -497,6 +497,7 @@ Stage2DArgs<TS> stage_args(const AdjointCall& c, const Work& w, StateBuf<TS> in,
   a.gamma = c.gamma; a.cfl = 0.3; a.dt_override = dt; a.limiter = c.limiter;
   a.gas.set(c.gamma);
   a.in = in; a.base = base; a.out = out;
+  a.lim_sl = nullptr;
   a.ctl = w.ctl;
   return a;
 }

@@ -79,6 +79,7 @@ __device__ __forceinline__ Stage2DArgs<TS> problem_args(const BatchArgs<TS>& B, 
   a.base.sl = B.sl[0] + p.sl_off;
   a.out.c0 = B.c0[out] + p.c0_off;
   a.out.sl = B.sl[out] + p.sl_off;
+  a.lim_sl = B.sl[2] + p.sl_off;  // the step's output buffer
   a.ctl = B.ctl + ip;
   return a;
 }

@@ -222,7 +222,8 @@ cudaError_t launch_batch_step_t(dg_ctx* c, int a, int b, double dtov) {
 }
 
 template <class TS>
-cudaError_t launch_stage_t(dg_ctx* c, int stage, int in, int base, int out, double dtov) {
+cudaError_t launch_stage_t(dg_ctx* c, int stage, int in, int base, int out, double dtov,
+                           int lim) {
   for (size_t ip = 0; ip < c->probs.size(); ++ip) {
     const Prob& p = c->probs[ip];
     if (c->dim == 2) {
@@ -234,6 +235,7 @@ cudaError_t launch_stage_t(dg_ctx* c, int stage, int in, int base, int out, doub
       a.in = sbuf<TS>(c, in, p);
       a.base = sbuf<TS>(c, base, p);
       a.out = sbuf<TS>(c, out, p);
+      a.lim_sl = lim >= 0 ? sbuf<TS>(c, lim, p).sl : nullptr;
       a.ctl = c->ctl + ip;
       cudaError_t e = launch_stage2d(c->eq, c->variant < 0 ? 0 : c->variant, stage, a,
                                      c->launch_stream);
@@ -247,6 +249,7 @@ cudaError_t launch_stage_t(dg_ctx* c, int stage, int in, int base, int out, doub
       a.in = sbuf<TS>(c, in, p);
       a.base = sbuf<TS>(c, base, p);
       a.out = sbuf<TS>(c, out, p);
+      a.lim_sl = lim >= 0 ? sbuf<TS>(c, lim, p).sl : nullptr;
       a.ctl = c->ctl + ip;
       cudaError_t e = launch_stage3d(c->variant < 0 ? 0 : c->variant, stage, a, c->launch_stream);
       if (e != cudaSuccess) return e;
@@ -255,18 +258,20 @@ cudaError_t launch_stage_t(dg_ctx* c, int stage, int in, int base, int out, doub
   return cudaSuccess;
 }
 
-cudaError_t launch_stage(dg_ctx* c, int stage, int in, int base, int out, double dtov) {
-  return c->fp32 ? launch_stage_t<float>(c, stage, in, base, out, dtov)
-                 : launch_stage_t<double>(c, stage, in, base, out, dtov);
+// `lim`: buffer receiving the limited derivative coefficients of the step input
+// (the step's output buffer), or -1.
+cudaError_t launch_stage(dg_ctx* c, int stage, int in, int base, int out, double dtov, int lim) {
+  return c->fp32 ? launch_stage_t<float>(c, stage, in, base, out, dtov, lim)
+                 : launch_stage_t<double>(c, stage, in, base, out, dtov, lim);
 }
 
 // One SSP-RK2 step from buffer `a` into buffer `b` (buffer 1 holds V^1).
 cudaError_t launch_step(dg_ctx* c, int a, int b, double dtov) {
   if (c->batch2d)
     return c->fp32 ? launch_batch_step_t<float>(c, a, b, dtov) : launch_batch_step_t<double>(c, a, b, dtov);
-  cudaError_t e = launch_stage(c, 1, a, a, 1, dtov);
+  cudaError_t e = launch_stage(c, 1, a, a, 1, dtov, b);
   if (e != cudaSuccess) return e;
-  return launch_stage(c, 2, 1, a, b, dtov);
+  return launch_stage(c, 2, 1, a, b, dtov, b);
 }
 
 cudaError_t launch_step_profiled(dg_ctx* c, int a, int b, double dtov) {
@@ -287,7 +292,7 @@ cudaError_t launch_step_profiled(dg_ctx* c, int a, int b, double dtov) {
     cudaEventCreate(&ev.a);
     cudaEventCreate(&ev.b);
     cudaEventRecord(ev.a, c->stream);
-    cudaError_t e = s == 1 ? launch_stage(c, 1, a, a, 1, dtov) : launch_stage(c, 2, 1, a, b, dtov);
+    cudaError_t e = s == 1 ? launch_stage(c, 1, a, a, 1, dtov, b) : launch_stage(c, 2, 1, a, b, dtov, b);
     cudaEventRecord(ev.b, c->stream);
     c->evs.push_back(ev);
     if (e != cudaSuccess) return e;

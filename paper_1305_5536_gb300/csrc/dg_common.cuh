@@ -58,6 +58,10 @@ struct Stage2DArgs {
   StateBuf<TS> in;    // stage input (V^n in stage 1, V^1 in stage 2)
   StateBuf<TS> base;  // V^n (stage 2 only)
   StateBuf<TS> out;
+  // Limited derivative coefficients of U^n = Lambda(V^n): stage 1 stores those of
+  // its own cells here (the step's output buffer), stage 2 reads them back for its
+  // own cell before overwriting it.  Null: stage 2 recomputes them.
+  TS* lim_sl;
   Ctl* ctl;
 };
 
@@ -73,6 +77,7 @@ struct Stage3DArgs {
   StateBuf<TS> in;
   StateBuf<TS> base;
   StateBuf<TS> out;
+  TS* lim_sl;  // as for Stage2DArgs
   Ctl* ctl;
 };
 

@@ -451,14 +451,24 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
     for (int v = 0; v < NV; ++v) o0[v] = fma(dt, Cvt<TC>::to_f64(rc0[v]), A.in.c0[v * ncell + gc]);
 #pragma unroll
     for (int k = 0; k < NS; ++k) os[k] = s[k] + dtc * rs[k];
+    if (A.limiter && A.lim_sl && owner) {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) A.lim_sl[k * ncell + gc] = (TS)s[k];
+    }
   } else {
     // V^{n+1} = 1/2 U^n + 1/2 (U^1 + dt L(U^1)), U^n = limited V^n of this cell
     TC cn[NV], sn[NS];
 #pragma unroll
     for (int v = 0; v < NV; ++v) cn[v] = Cvt<TC>::to_tc(A.base.c0[v * ncell + gc]);
+    if (A.limiter && A.lim_sl) {
+      // limited by stage 1 of this step
 #pragma unroll
-    for (int k = 0; k < NS; ++k) sn[k] = (TC)A.base.sl[k * ncell + gc];
-    if (A.limiter) {
+      for (int k = 0; k < NS; ++k) sn[k] = (TC)A.lim_sl[k * ncell + gc];
+    } else {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) sn[k] = (TC)A.base.sl[k * ncell + gc];
+    }
+    if (A.limiter && !A.lim_sl) {
       TC W[NP], Wn[4][NP];
       prims2d<EQ, TC>(G, cn, W, err);
       const size_t nb[4] = {(size_t)s_gy[ly + 2] + s_gx[lx + 1], (size_t)s_gy[ly + 2] + s_gx[lx + 3],

@@ -364,11 +364,20 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs
     for (int v = 0; v < 5; ++v) o0[v] = fma(dt, Cvt<TC>::to_f64(rc0[v]), A.in.c0[v * ncell + gc]);
 #pragma unroll
     for (int k = 0; k < 15; ++k) os[k] = s[k] + dtc * rs[k];
+    if (A.limiter && A.lim_sl && owner) {
+#pragma unroll
+      for (int k = 0; k < 15; ++k) A.lim_sl[k * ncell + gc] = (TS)s[k];
+    }
   } else {
     TC sn[15];
+    if (A.limiter && A.lim_sl) {
 #pragma unroll
-    for (int k = 0; k < 15; ++k) sn[k] = (TC)A.base.sl[k * ncell + gc];
-    if (A.limiter) {
+      for (int k = 0; k < 15; ++k) sn[k] = (TC)A.lim_sl[k * ncell + gc];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 15; ++k) sn[k] = (TC)A.base.sl[k * ncell + gc];
+    }
+    if (A.limiter && !A.lim_sl) {
       TC c[5], W[5], Wn[6][5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) c[v] = Cvt<TC>::to_tc(A.base.c0[v * ncell + gc]);
