@@ -75,7 +75,8 @@ def _src_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1305_5536_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.startswith("dg_stage") or f == "dg_physics.cuh" or f == "dg_common.cuh":
+        if f.startswith("dg_stage") or f in ("dg_physics.cuh", "dg_common.cuh", "dg_tma.cuh",
+                                             "dg_batch.cu"):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -231,6 +232,7 @@ def run_gpu(args):
         s.profile(False)
         tot = max_over_ranks(sum(step_ms), "cuda")
         res = dict(ms_total=tot, ms_per_step=tot / K, kernel_ms=kms, kernel_launches=kn,
+                   kernel=s.kernel_name(),
                    bytes=[s.stage_bytes(1), s.stage_bytes(2)], wall_s=t_wall,
                    clocks=sampler.summary() if sampler else None)
         # end to end through the public API with host buffers (pinned)
@@ -263,10 +265,7 @@ def run_gpu(args):
     k = 1 if r32["kernel_ms"][1] >= r32["kernel_ms"][0] else 0
     avg_ms = r32["kernel_ms"][k] / max(r32["kernel_launches"][k], 1)
     achieved = r32["bytes"][k] / (avg_ms * 1e-3) / 1e9
-    kname = ("stage2d_kernel<%s,float,float,stage%d>" % (W["eq"], k + 1) if W["dim"] == 2
-             else "stage3d_kernel<float,float,stage%d>" % (k + 1))
-    if sizes is not None:
-        kname = "batch2d_kernel<%s,float,float> (both stages)" % W["eq"]
+    kname = "%s %s, stage %s" % (r32["kernel"], W["eq"], "1+2" if sizes is not None else k + 1)
     traffic = _traffic(kname, args.workload)
     v64 = ws * ncell / (r64["ms_per_step"] * 1e-3)
     out = {
@@ -297,7 +296,7 @@ def run_gpu(args):
         "fp64": {"value": v64, "ms_per_step": r64["ms_per_step"],
                  "speedup_fp32_over_fp64": v64 and value / v64,
                  "stage_ms_avg": [r64["kernel_ms"][i] / max(r64["kernel_launches"][i], 1)
-                                  for i in range(2)]},
+                                  for i in range(2)], "kernel": r64["kernel"]},
         "e2e": {"value": ws * ncell / (r32["e2e_ms_per_step"] * 1e-3), "unit": "cell-updates/s",
                 "h2d_bytes_per_step": r32["e2e_bytes"], "d2h_bytes_per_step": r32["e2e_bytes"]},
         "gpu_launches": int(sum(r32["kernel_launches"])),

@@ -186,6 +186,11 @@ dg_status dg_profile(dg_ctx* ctx, int enable);
  * runs both stages in one launch per step, counted under k = 1.  Synchronises. */
 dg_status dg_profile_read(dg_ctx* ctx, double ms[2], long long launches[2]);
 
+/* Name of the stage kernel and tile shape this context launches (chosen by the
+ * autotuner when the state is first set), e.g. "stage2d_tma_kernel 16x16 fp32".
+ * Owned by the context. */
+const char* dg_kernel_name(const dg_ctx* ctx);
+
 /* Algorithmic DRAM bytes of one stage-kernel launch on the whole grid (all
  * problems): stage 1 reads and writes one state, stage 2 reads two and writes
  * one (a batch of 2D problems: 0 for stage 1, both stages for stage 2).  Used for

@@ -76,6 +76,7 @@ struct dg_ctx {
   unsigned* bar = nullptr;
   long long spin_limit = 1LL << 24;
   int extra_arrivals = 0;
+  std::string kname;
 };
 
 namespace {
@@ -790,6 +791,24 @@ dg_status dg_profile_read(dg_ctx* c, double ms[2], long long launches[2]) {
     launches[e.kind] += c->batch2d ? 1 : (long long)c->probs.size();
   }
   return DG_OK;
+}
+
+const char* dg_kernel_name(const dg_ctx* cc) {
+  if (!cc) return "";
+  dg_ctx* c = const_cast<dg_ctx*>(cc);
+  const int v = c->variant < 0 ? 0 : c->variant;
+  const char* prec = c->fp32 ? "fp32" : "fp64";
+  char b[96];
+  if (c->batch2d)
+    snprintf(b, sizeof(b), "batch2d_kernel %dx%d %s", batch2d_tile_x(c->fp32, v),
+             batch2d_tile_y(c->fp32, v), prec);
+  else if (c->dim == 2)
+    snprintf(b, sizeof(b), "%s %s %s", v >= 3 ? "stage2d_tma_kernel" : "stage2d_kernel",
+             stage2d_variant_name(c->eq, c->fp32, v), prec);
+  else
+    snprintf(b, sizeof(b), "stage3d_kernel %s %s", stage3d_variant_name(c->fp32, v), prec);
+  c->kname = b;
+  return c->kname.c_str();
 }
 
 double dg_stage_bytes(const dg_ctx* c, int stage) {

@@ -12,6 +12,10 @@ import numpy as np
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libdg.so")
+# Tile shapes chosen by the library's autotuner, per (equations, dimension,
+# precision, grid): the shipped cache makes runs reproducible; DG_TUNE_CACHE
+# names another file.
+TUNE_CACHE = os.path.join(PKG, "tune_cache.txt")
 
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONPHYS, DG_ETIMEOUT, DG_ESTATE = range(7)
 DG_EULER, DG_MHD = 0, 1
@@ -24,7 +28,7 @@ _STATUS = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_ENO
 SYMBOLS = ["dg_num_planes", "dg_init", "dg_init_batch", "dg_destroy", "dg_last_error",
            "dg_set_state", "dg_get_state", "dg_step", "dg_sync", "dg_get_times", "dg_totals",
            "dg_divb", "dg_adjoint_step", "dg_record", "dg_adjoint", "dg_profile",
-           "dg_profile_read", "dg_stage_bytes", "dg_totals_noalloc"]
+           "dg_profile_read", "dg_stage_bytes", "dg_totals_noalloc", "dg_kernel_name"]
 
 
 class DGError(RuntimeError):
@@ -55,6 +59,7 @@ def load():
     if not os.path.exists(LIB_PATH):
         raise RuntimeError("libdg.so is missing: the CUDA extension must be built "
                            "(python -c 'import __graft_entry__ as g; g.build()')")
+    os.environ.setdefault("DG_TUNE_CACHE", TUNE_CACHE)
     L = ctypes.CDLL(LIB_PATH)
     P, c_int, c_double = ctypes.POINTER, ctypes.c_int, ctypes.c_double
     vp = ctypes.c_void_p
@@ -81,6 +86,8 @@ def load():
     L.dg_stage_bytes.argtypes = [vp, c_int]
     L.dg_stage_bytes.restype = c_double
     L.dg_totals_noalloc.argtypes = [pcfg, vp, vp, c_int, vp]
+    L.dg_kernel_name.argtypes = [vp]
+    L.dg_kernel_name.restype = ctypes.c_char_p
     _lib = L
     return L
 
@@ -247,6 +254,9 @@ class DGSolver:
         n = (ctypes.c_longlong * 2)()
         self._check(self._L.dg_profile_read(self._h, ms, n))
         return [ms[0], ms[1]], [n[0], n[1]]
+
+    def kernel_name(self):
+        return self._L.dg_kernel_name(self._h).decode()
 
     def stage_bytes(self, stage):
         return self._L.dg_stage_bytes(self._h, int(stage))
