@@ -48,6 +48,10 @@ def lib():
         L.oracle_cfl_dt.argtypes = [pc, pd, d, P(i)]
         L.oracle_cfl_dt.restype = d
         L.oracle_run.argtypes = [pc, pd, pd, i, d, d, pd]
+        L.oracle_mh_step.argtypes = [pc, pd, pd, d, i]
+        L.oracle_mh_run.argtypes = [pc, pd, pd, i, d, d, i, pd]
+        L.oracle_prim_rates.argtypes = [pd, pd, i, d, pd]
+        L.oracle_prim_rates.restype = None
         L.oracle_tangent_step.argtypes = [pc, pd, pd, pd, pd, d]
         L.oracle_tangent_rhs.argtypes = [pc, pd, pd, pd, pd]
         L.oracle_tangent_limit.argtypes = [pc, pd, pd, pd, pd]
@@ -119,6 +123,24 @@ class Problem:
         dts = np.zeros(max(nsteps, 1))
         f = lib().oracle_run(ctypes.byref(self._c), _p(u), _p(out), int(nsteps), float(cfl),
                              float(dt), _p(dts))
+        return out, dts[:nsteps], f
+
+    def mh_step(self, u, dt, face_points=1):
+        """One MUSCL-Hancock step (Sec. 2.4) with time step dt; face_points 1 = the
+        face-centroid flux of eq. `GalerkUpdate`, 2 = the Gauss rule of the RK step."""
+        u = self._chk(u)
+        out = np.empty_like(u)
+        f = lib().oracle_mh_step(ctypes.byref(self._c), _p(u), _p(out), float(dt),
+                                 int(face_points))
+        return out, f
+
+    def mh_run(self, u, nsteps, cfl=0.3, dt=0.0, face_points=1):
+        """nsteps MUSCL-Hancock steps (Courant time step unless dt > 0)."""
+        u = self._chk(u)
+        out = np.empty_like(u)
+        dts = np.zeros(max(nsteps, 1))
+        f = lib().oracle_mh_run(ctypes.byref(self._c), _p(u), _p(out), int(nsteps), float(cfl),
+                                float(dt), int(face_points), _p(dts))
         return out, dts[:nsteps], f
 
     def limit(self, u):
@@ -214,3 +236,13 @@ def phys_flux(U, d, gamma):
     F = np.zeros(8)
     lib().oracle_phys_flux(_p(U), int(d), float(gamma), _p(F))
     return F
+
+
+def prim_rates(W, dW, dim, gamma):
+    """dW/dt = -sum_d A_d(W) dW/dx_d (primitive form used by the MUSCL-Hancock
+    prediction); W (8,), dW (8, 3)."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    dW = np.ascontiguousarray(dW, dtype=np.float64).reshape(8, 3)
+    out = np.zeros(8)
+    lib().oracle_prim_rates(_p(W), _p(dW), int(dim), float(gamma), _p(out))
+    return out

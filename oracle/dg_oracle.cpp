@@ -15,7 +15,10 @@
 // The time integrator is the two-stage strong-stability-preserving Runge-Kutta
 // method (the "traditional DG" integrator named in Sec. 2.4) and faces are
 // integrated with 2-point Gauss rules per face dimension; volumes with 2^dim
-// tensor Gauss points.
+// tensor Gauss points.  A second integrator, the MUSCL-Hancock step of Sec. 2.4
+// (half-step prediction of primitive values, one update by eq. `GalerkUpdate`),
+// integrates faces with one point at the face centroid (the paper's form) or the
+// same 2-point Gauss rules.
 //
 // Everything is written as the generic weak form: for every basis function W the
 // face integral of F.n W and the volume integral of F . grad W are evaluated by
@@ -675,6 +678,43 @@ int numerical_flux(const Cfg& c, const R UL[8], const R UR[8], int d, R F[8]) {
 // The magnetic field shares one alpha = min(alpha_Bx, alpha_By) for (a1, a2, a3),
 // which keeps each cell's field divergence free.
 // ------------------------------------------------------------------------------
+// Gradients dU[q][d] of the conserved variables of one cell's polynomial: its
+// Taylor derivative coefficients and, for MHD, the derivatives of the magnetic
+// basis expansion, dBx = (a3, a1), dBy = (a2, -a3).
+template <class R>
+void conserved_gradients(const Grid& G, const R* u, long c, R dU[8][3]) {
+  const long n = G.ncell;
+  const int b0 = G.L.nT * G.L.nK;
+  for (int q = 0; q < 8; ++q) for (int d = 0; d < 3; ++d) dU[q][d] = R(0.0);
+  for (int v = 0; v < G.L.nT; ++v)
+    for (int d = 0; d < G.c.dim; ++d) dU[G.L.tvar[v]][d] = u[(long)(v * G.L.nK + 1 + d) * n + c];
+  if (G.L.nB) {
+    R a1 = u[(long)(b0 + 2) * n + c], a2 = u[(long)(b0 + 3) * n + c],
+      a3 = u[(long)(b0 + 4) * n + c];
+    dU[I_BX][0] = a3; dU[I_BX][1] = a1;
+    dU[I_BY][0] = a2; dU[I_BY][1] = -a3;
+  }
+}
+
+// Primitive gradients dW[q][d] at centroid primitives W by the product rule
+// (Sec. 2.2, the expansion below eq. `GalerkUpdate`):
+//   dv = (dm - v drho)/rho,  dp = (gamma-1)(dE - v^2/2 drho - rho v.dv - B.dB).
+template <class R>
+void primitive_gradients(const R W[8], const R dU[8][3], double g, R dW[8][3]) {
+  for (int d = 0; d < 3; ++d) {
+    dW[0][d] = dU[I_RHO][d];
+    R vdv(0.0), BdB(0.0);
+    for (int i = 0; i < 3; ++i) {
+      dW[1 + i][d] = (dU[1 + i][d] - W[1 + i] * dU[I_RHO][d]) / W[0];
+      vdv = vdv + W[1 + i] * dW[1 + i][d];
+      dW[5 + i][d] = dU[5 + i][d];
+      BdB = BdB + W[5 + i] * dU[5 + i][d];
+    }
+    R v2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
+    dW[4][d] = (g - 1.0) * (dU[I_E][d] - 0.5 * v2 * dU[I_RHO][d] - W[0] * vdv - BdB);
+  }
+}
+
 template <class R>
 void limit_state(const Grid& G, const R* u, R* out, int& flags) {
   const long n = G.ncell;
@@ -700,31 +740,9 @@ void limit_state(const Grid& G, const R* u, R* out, int& flags) {
   for (long c = 0; c < n; ++c) {
     R W[8];
     for (int q = 0; q < 8; ++q) W[q] = prim[(size_t)q * n + c];
-    // gradients of conserved variables: dU[q][d]
-    R dU[8][3];
-    for (int q = 0; q < 8; ++q) for (int d = 0; d < 3; ++d) dU[q][d] = R(0.0);
-    for (int v = 0; v < G.L.nT; ++v)
-      for (int d = 0; d < dim; ++d) dU[G.L.tvar[v]][d] = u[(long)(v * G.L.nK + 1 + d) * n + c];
-    if (mhd) {
-      R a1 = u[(long)(b0 + 2) * n + c], a2 = u[(long)(b0 + 3) * n + c],
-        a3 = u[(long)(b0 + 4) * n + c];
-      dU[I_BX][0] = a3; dU[I_BX][1] = a1;
-      dU[I_BY][0] = a2; dU[I_BY][1] = -a3;
-    }
-    // primitive gradients dW[q][d]
-    R dW[8][3];
-    for (int d = 0; d < 3; ++d) {
-      dW[0][d] = dU[I_RHO][d];
-      R vdv(0.0), BdB(0.0);
-      for (int i = 0; i < 3; ++i) {
-        dW[1 + i][d] = (dU[1 + i][d] - W[1 + i] * dU[I_RHO][d]) / W[0];
-        vdv = vdv + W[1 + i] * dW[1 + i][d];
-        dW[5 + i][d] = dU[5 + i][d];
-        BdB = BdB + W[5 + i] * dU[5 + i][d];
-      }
-      R v2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
-      dW[4][d] = (g - 1.0) * (dU[I_E][d] - 0.5 * v2 * dU[I_RHO][d] - W[0] * vdv - BdB);
-    }
+    R dU[8][3], dW[8][3];
+    conserved_gradients(G, u, c, dU);
+    primitive_gradients(W, dU, g, dW);
     // limiter coefficient of each primitive variable
     auto alpha_of = [&](int q) {
       R phimax = W[q], phimin = W[q];
@@ -1036,6 +1054,206 @@ inline double cfl_dt(const Grid& G, const double* u, double cfl, int& flags) {
   return smax > 0.0 ? cfl / smax : 0.0;
 }
 
+// ------------------------------------------------------------------------------
+// MUSCL-Hancock step (Sec. 2.4, "Time stepping"), the paper's own integrator.
+//   1. Limit at the beginning of the step (Sec. 2.5) and recompute the conserved
+//      derivative coefficients from the limited primitive gradients.
+//   2. Predict primitive values half a step ahead from the centroid values and
+//      their gradients, W(x, t + dt/2) = W_c + grad W . x + dt/2 dW/dt, with the
+//      time derivative from the primitive form of eq. `cons` at the centroid.
+//   3. Riemann fluxes between the predicted face values of both sides (Sec. 2.3;
+//      MHD with the averaged normal field of Sec. 2.6), and volume fluxes of the
+//      predicted state at the volume Gauss points ("the same prediction
+//      equations" in the volume integral of eq. `GalerkUpdate`).
+//   4. One update of the moments Q = int U and R = M grad U (eq. `GalerkUpdate`):
+//      Q^{n+1} = Q^n - dt sum_f A_f F_f,
+//      R^{n+1} = R^n - dt sum_f A_f F_f c_f + dt int F dOmega,
+//      written, as in dg_rhs, as the weak form of every basis function with the
+//      face integral taken by a face quadrature rule: one point at the face
+//      centroid c_f with weight A_f (eq. `GalerkUpdate`), or the 2-point Gauss
+//      rule per face dimension.
+// ------------------------------------------------------------------------------
+
+// Primitive form of eq. `cons` along axis d: dW/dt = - sum_d A_d(W) dW/dx_d for
+// W = (rho, v, p, B), i.e.
+//   drho/dt = -v.grad rho - rho div v
+//   dv/dt   = -(v.grad) v - grad p / rho - (grad(B^2/2) - (B.grad) B) / rho
+//   dp/dt   = -v.grad p - gamma p div v
+//   dB/dt   = (B.grad) v - (v.grad) B - B div v
+// (terms proportional to div B are left out: every cell's field is divergence
+// free, Sec. 2.2, and the limiter keeps it so).  Row r, column k of A_d.
+inline void prim_matrix(const double W[8], int d, double g, double A[8][8]) {
+  for (int r = 0; r < 8; ++r) for (int k = 0; k < 8; ++k) A[r][k] = 0.0;
+  const double rho = W[0], p = W[4];
+  const double* v = W + 1;
+  const double* B = W + 5;
+  A[0][0] = v[d];
+  A[0][1 + d] = rho;
+  for (int i = 0; i < 3; ++i) {
+    A[1 + i][1 + i] = v[d];
+    if (i == d) {
+      A[1 + i][4] = 1.0 / rho;
+      for (int j = 0; j < 3; ++j) A[1 + i][5 + j] += B[j] / rho;  // grad_d (B^2/2)
+    }
+    A[1 + i][5 + i] -= B[d] / rho;  // -(B_d d/dx_d) B_i
+  }
+  A[4][4] = v[d];
+  A[4][1 + d] = g * p;
+  for (int i = 0; i < 3; ++i) {
+    A[5 + i][1 + i] -= B[d];  // (B_d d/dx_d) v_i
+    A[5 + i][5 + i] += v[d];  // (v_d d/dx_d) B_i
+    A[5 + i][1 + d] += B[i];  // B_i dv_d/dx_d
+  }
+}
+
+inline void prim_rates(const double W[8], const double dW[8][3], int dim, double g,
+                       double Wt[8]) {
+  for (int r = 0; r < 8; ++r) Wt[r] = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    double A[8][8];
+    prim_matrix(W, d, g, A);
+    for (int r = 0; r < 8; ++r)
+      for (int k = 0; k < 8; ++k) Wt[r] -= A[r][k] * dW[k][d];
+  }
+}
+
+// Face rule with `npts` points: 1 = the face centroid with weight A_f, else the
+// 2-point Gauss rule per face dimension (face_quad).
+inline FaceQuad face_quad_n(const Grid& G, int d, int s, int npts) {
+  if (npts != 1) return face_quad(G, d, s);
+  FaceQuad F;
+  F.ng = 1;
+  F.x[0][0] = F.x[0][1] = F.x[0][2] = 0.0;
+  F.x[0][d] = 0.5 * s * G.h[d];
+  F.w[0] = G.vol / G.h[d];
+  return F;
+}
+
+int mh_step(const Grid& G, const double* vn, double* vout, double dt, int face_points) {
+  const long n = G.ncell;
+  const int dim = G.c.dim;
+  const double g = G.c.gamma;
+  const bool mhd = G.L.nB > 0;
+  const int nT = G.L.nT, nK = G.L.nK, b0 = nT * nK;
+  const long tot = (long)G.L.nplanes * n;
+  const Mass M = mass_matrices(G);
+  const VolQuad VQ = vol_quad(G);
+  int flags = 0;
+
+  // 1. limited state U^n
+  std::vector<double> un(tot);
+  limit_state<double>(G, vn, un.data(), flags);
+
+  // 2. predicted centroid primitives Wp = W_c + dt/2 dW/dt and the primitive
+  //    gradients dW of every cell
+  std::vector<double> Wp((size_t)8 * n), dW((size_t)24 * n);
+  for (long c = 0; c < n; ++c) {
+    const double x0[3] = {0.0, 0.0, 0.0};
+    double U[8], W[8], dUc[8][3], dWc[8][3], Wt[8];
+    eval_poly<double>(G, un.data(), c, x0, U);
+    cons_to_prim(U, g, W);
+    if (!(W[0] > 0.0 && W[4] > 0.0)) flags |= FLAG_NONPHYS;
+    conserved_gradients<double>(G, un.data(), c, dUc);
+    primitive_gradients<double>(W, dUc, g, dWc);
+    prim_rates(W, dWc, dim, g, Wt);
+    for (int q = 0; q < 8; ++q) {
+      Wp[(size_t)q * n + c] = W[q] + 0.5 * dt * Wt[q];
+      for (int e = 0; e < 3; ++e) dW[((size_t)q * 3 + e) * n + c] = dWc[q][e];
+    }
+  }
+  // predicted primitive state of cell c at local point x
+  auto predict = [&](long c, const double x[3], double W[8]) {
+    for (int q = 0; q < 8; ++q) {
+      double s = Wp[(size_t)q * n + c];
+      for (int e = 0; e < dim; ++e) s += dW[((size_t)q * 3 + e) * n + c] * x[e];
+      W[q] = s;
+    }
+    if (!(W[0] > 0.0 && W[4] > 0.0)) flags |= FLAG_NONPHYS;
+  };
+
+  // 3a. Riemann fluxes at the face points, each face once (stored with its
+  //     left cell, as in dg_rhs)
+  std::vector<double> Fh[3];
+  FaceQuad FQp[3], FQm[3];
+  for (int d = 0; d < dim; ++d) {
+    FQp[d] = face_quad_n(G, d, +1, face_points);
+    FQm[d] = face_quad_n(G, d, -1, face_points);
+    Fh[d].assign((size_t)n * FQp[d].ng * 8, 0.0);
+    for (long c = 0; c < n; ++c) {
+      long r = G.nbr(c, d, +1);
+      for (int gp = 0; gp < FQp[d].ng; ++gp) {
+        double WL[8], WR[8], UL[8], UR[8], F[8];
+        predict(c, FQp[d].x[gp], WL);
+        predict(r, FQm[d].x[gp], WR);
+        if (mhd) {
+          double bn = 0.5 * (WL[5 + d] + WR[5 + d]);
+          WL[5 + d] = bn;
+          WR[5 + d] = bn;
+        }
+        prim_to_cons(WL, g, UL);
+        prim_to_cons(WR, g, UR);
+        flags |= numerical_flux(G.c, UL, UR, d, F);
+        for (int q = 0; q < 8; ++q) Fh[d][((size_t)c * FQp[d].ng + gp) * 8 + q] = F[q];
+      }
+    }
+  }
+
+  // 3b, 4. per cell: face and volume integrals of every basis function, mass
+  //        matrix solve, update of the limited coefficients
+  for (long c = 0; c < n; ++c) {
+    double bT[5][4], bB[5];
+    for (int v = 0; v < 5; ++v) for (int k = 0; k < 4; ++k) bT[v][k] = 0.0;
+    for (int k = 0; k < 5; ++k) bB[k] = 0.0;
+    for (int d = 0; d < dim; ++d)
+      for (int s = -1; s <= 1; s += 2) {
+        const FaceQuad& FQ = s > 0 ? FQp[d] : FQm[d];
+        long owner = s > 0 ? c : G.nbr(c, d, -1);
+        for (int gp = 0; gp < FQ.ng; ++gp) {
+          const double* F = &Fh[d][((size_t)owner * FQ.ng + gp) * 8];
+          const double w = FQ.w[gp] * s;
+          for (int v = 0; v < nT; ++v)
+            for (int k = 0; k < nK; ++k)
+              bT[v][k] -= w * taylor_w(k, FQ.x[gp]) * F[G.L.tvar[v]];
+          if (mhd)
+            for (int k = 0; k < 5; ++k) {
+              double wk[2];
+              mag_w(k, FQ.x[gp], wk);
+              bB[k] -= w * (wk[0] * F[I_BX] + wk[1] * F[I_BY]);
+            }
+        }
+      }
+    for (int q = 0; q < VQ.nq; ++q) {
+      double W[8], U[8];
+      predict(c, VQ.x[q], W);
+      prim_to_cons(W, g, U);
+      for (int d = 0; d < dim; ++d) {
+        double F[8];
+        phys_flux(U, d, g, F);
+        for (int v = 0; v < nT; ++v)
+          for (int k = 0; k < nK; ++k) bT[v][k] += VQ.w[q] * taylor_dw(k, d) * F[G.L.tvar[v]];
+        if (mhd)
+          for (int k = 0; k < 5; ++k)
+            bB[k] += VQ.w[q] * (mag_dw(k, 0, d) * F[I_BX] + mag_dw(k, 1, d) * F[I_BY]);
+      }
+    }
+    for (int v = 0; v < nT; ++v)
+      for (int k = 0; k < nK; ++k) {
+        double s = 0.0;
+        for (int l = 0; l < nK; ++l) s += M.MTinv[k * nK + l] * bT[v][l];
+        const long i = (long)(v * nK + k) * n + c;
+        vout[i] = un[i] + dt * s;
+      }
+    if (mhd)
+      for (int k = 0; k < 5; ++k) {
+        double s = 0.0;
+        for (int l = 0; l < 5; ++l) s += M.MBinv[k * 5 + l] * bB[l];
+        const long i = (long)(b0 + k) * n + c;
+        vout[i] = un[i] + dt * s;
+      }
+  }
+  return flags;
+}
+
 }  // namespace oracle
 
 // ==============================================================================
@@ -1091,6 +1309,37 @@ int oracle_run(const Cfg* c, const double* u, double* out, int nsteps, double cf
   }
   std::copy(a.begin(), a.end(), out);
   return flags;
+}
+
+// One MUSCL-Hancock step (face_points 1: face centroid, 2: Gauss rule).
+int oracle_mh_step(const Cfg* c, const double* u, double* out, double dt, int face_points) {
+  Grid G(*c);
+  return mh_step(G, u, out, dt, face_points);
+}
+
+// nsteps MUSCL-Hancock steps, as oracle_run.
+int oracle_mh_run(const Cfg* c, const double* u, double* out, int nsteps, double cfl,
+                  double dt_fixed, int face_points, double* dts) {
+  Grid G(*c);
+  const long tot = (long)G.L.nplanes * G.ncell;
+  std::vector<double> a(u, u + tot), b(tot);
+  int flags = 0;
+  for (int s = 0; s < nsteps; ++s) {
+    double dt = dt_fixed > 0.0 ? dt_fixed : cfl_dt(G, a.data(), cfl, flags);
+    if (dts) dts[s] = dt;
+    flags |= mh_step(G, a.data(), b.data(), dt, face_points);
+    std::swap(a, b);
+  }
+  std::copy(a.begin(), a.end(), out);
+  return flags;
+}
+
+// Time derivative of the primitives W (8) with gradients dW ([8][3], row-major)
+// from the primitive form used by the MUSCL-Hancock prediction.
+void oracle_prim_rates(const double* W, const double* dW, int dim, double gamma, double* Wt) {
+  double G3[8][3];
+  for (int q = 0; q < 8; ++q) for (int e = 0; e < 3; ++e) G3[q][e] = dW[q * 3 + e];
+  prim_rates(W, G3, dim, gamma, Wt);
 }
 
 // Tangent of one step with the time step held fixed: out = step(u),
