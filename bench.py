@@ -41,6 +41,10 @@ WORKLOADS = {
     "kh3d_128": dict(eq="euler", dim=3, n=(128, 128, 128), desc=(
         "3D Euler Kelvin-Helmholtz shear layer 128^3 (profiling size), exact Riemann, limiter, "
         "CFL 0.3")),
+    "orszag_tang_512_mh": dict(eq="mhd", dim=2, n=(512, 512), integrator="mh", desc=(
+        "2D ideal MHD Orszag-Tang vortex 512x512, P1 DG, div-free B basis, HLLD, "
+        "min/max limiter, CFL 0.3, MUSCL-Hancock step (Sec. 2.4) with one flux at each "
+        "face centroid")),
     "mhd_batch64": dict(eq="mhd", dim=2, n=None, desc=(
         "64 independent 2D ideal-MHD problems, N log-uniform in [32, 512] (seeded), "
         "random-phase smooth v and div-free B, one persistent launch per step, CFL 0.3")),
@@ -196,7 +200,8 @@ def run_gpu(args):
         if sizes is not None:
             return dg.DGSolver(configs=[dg.make_config(W["eq"], 2, (N, N), precision=prec)
                                         for N in sizes])
-        return dg.DGSolver(W["eq"], W["dim"], W["n"], precision=prec, cfl=0.3)
+        return dg.DGSolver(W["eq"], W["dim"], W["n"], precision=prec, cfl=0.3,
+                           integrator=W.get("integrator", "rk2"))
 
     def measure(prec, K, Wm, with_clock):
         s = new_solver(prec)
@@ -260,16 +265,20 @@ def run_gpu(args):
     if rank != 0:
         return
     hbm, peak_kind = _peaks()
+    mh = W.get("integrator") == "mh"
     value = ws * ncell / (r32["ms_per_step"] * 1e-3)
     # dominant kernel by time: stage 2 (reads two states, writes one)
     k = 1 if r32["kernel_ms"][1] >= r32["kernel_ms"][0] else 0
     avg_ms = r32["kernel_ms"][k] / max(r32["kernel_launches"][k], 1)
     achieved = r32["bytes"][k] / (avg_ms * 1e-3) / 1e9
-    kname = "%s %s, stage %s" % (r32["kernel"], W["eq"], "1+2" if sizes is not None else k + 1)
+    if mh:
+        kname = "%s %s, step" % (r32["kernel"], W["eq"])
+    else:
+        kname = "%s %s, stage %s" % (r32["kernel"], W["eq"], "1+2" if sizes is not None else k + 1)
     traffic = _traffic(kname, args.workload)
     v64 = ws * ncell / (r64["ms_per_step"] * 1e-3)
     out = {
-        "metric": "DG cell-updates/sec (SSP-RK2 steps x cells / s)",
+        "metric": _metric(W),
         "value": value,
         "unit": "cell-updates/s",
         "n_gpus": ws,
@@ -342,25 +351,34 @@ def _oracle_sample(workload, u0):
     return [(P, u0)], desc, int(np.prod(n))
 
 
-def _oracle_sweep(items, dts):
+def _metric(W):
+    kind = "MUSCL-Hancock" if W.get("integrator") == "mh" else "SSP-RK2"
+    return "DG cell-updates/sec (%s steps x cells / s)" % kind
+
+
+def _oracle_sweep(items, dts, mh=False):
+    if mh:
+        return [(P, P.mh_step(u, dt, face_points=1)[0]) for (P, u), dt in zip(items, dts)]
     return [(P, P.step(u, dt)[0]) for (P, u), dt in zip(items, dts)]
 
 
 def cpu_baseline(workload, u0, budget_s=12.0, max_steps=50):
-    """The CPU oracle, as it stands, on one host core: SSP-RK2 steps of the same
-    workload (or of a bounded part of it) until ~budget_s of CPU time."""
+    """The CPU oracle, as it stands, on one host core: steps of the same workload
+    (or of a bounded part of it) until ~budget_s of CPU time."""
     items, desc, ncell = _oracle_sample(workload, u0)
+    mh = WORKLOADS[workload].get("integrator") == "mh"
     dts = [P.cfl_dt(u)[0] for P, u in items]
     n = 0
     t0 = time.perf_counter()
     while n < max_steps:
-        items = _oracle_sweep(items, dts)
+        items = _oracle_sweep(items, dts, mh)
         n += 1
         if time.perf_counter() - t0 > budget_s:
             break
     el = time.perf_counter() - t0
     return {"value": n * ncell / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-            "sample": "%d SSP-RK2 steps, %s (%.1f s)" % (n, desc, el)}
+            "sample": "%d %s steps, %s (%.1f s)" % (n, "MUSCL-Hancock" if mh else "SSP-RK2",
+                                                    desc, el)}
 
 
 def run_reference(args):
@@ -370,22 +388,24 @@ def run_reference(args):
     W = WORKLOADS[args.workload]
     u0, _, _ = _workload_state(W)
     items, desc, ncell = _oracle_sample(args.workload, u0)
+    mh = W.get("integrator") == "mh"
     dts = [P.cfl_dt(u)[0] for P, u in items]
     for _ in range(args.warmup):
-        items = _oracle_sweep(items, dts)
+        items = _oracle_sweep(items, dts, mh)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        items = _oracle_sweep(items, dts)
+        items = _oracle_sweep(items, dts, mh)
     el = time.perf_counter() - t0
     v = args.steps * ncell / el
     print(json.dumps({
-        "impl": "reference", "metric": "DG cell-updates/sec (SSP-RK2 steps x cells / s)",
+        "impl": "reference", "metric": _metric(W),
         "value": v, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": W["desc"], "grid": list(W["n"]) if W["n"] else "batch"},
         "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d SSP-RK2 steps, %s" % (args.steps, desc)},
+                         "sample": "%d %s steps, %s" % (args.steps, "MUSCL-Hancock" if mh
+                                                        else "SSP-RK2", desc)},
         "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))
 

@@ -60,6 +60,12 @@ typedef enum {
 enum { DG_EULER = 0, DG_MHD = 1 };
 enum { DG_FP64 = 0, DG_FP32 = 1 }; /* FP32: FP32 arithmetic and slopes, FP64 averages */
 enum { DG_EXACT = 0, DG_HLLD = 1 };
+/* Time integrators: the two-stage SSP Runge-Kutta method with 2-point Gauss face
+ * rules, or the MUSCL-Hancock step of Sec. 2.4 (half-step prediction of the
+ * primitive values from the cell centroid and the limited gradients, then one
+ * update of the averages and moments by eq. `GalerkUpdate`: one kernel and one
+ * read and write of the state per step). */
+enum { DG_SSPRK2 = 0, DG_MUSCL_HANCOCK = 1 };
 
 typedef struct {
   int eq;           /* DG_EULER | DG_MHD (MHD: dim 2 only) */
@@ -72,6 +78,11 @@ typedef struct {
   int precision;    /* DG_FP64 | DG_FP32 */
   int riemann;      /* DG_EXACT (Euler) | DG_HLLD (MHD); must match eq */
   int ckpt_every;   /* adjoint checkpoint stride k (>= 1); 0 = no recording */
+  int integrator;   /* DG_SSPRK2 | DG_MUSCL_HANCOCK */
+  int face_points;  /* MUSCL-Hancock face rule: 1 (or 0) = one flux at the face
+                       centroid with weight the face area (eq. `GalerkUpdate`),
+                       2 = 2-point Gauss rule per face dimension; SSP-RK2 always
+                       uses the Gauss rule and needs 0 or 2 */
 } dg_config;
 
 /* Number of interchange planes of a configuration, or -1 if it is invalid. */
@@ -106,9 +117,10 @@ dg_status dg_set_state(dg_ctx* ctx, const double* coeffs, int on_device);
 /* Copy the current state out (interchange layout, float64).  Synchronises. */
 dg_status dg_get_state(dg_ctx* ctx, double* coeffs, int on_device);
 
-/* Advance `nsteps` SSP-RK2 steps.  dt_override > 0: every step uses that time
- * step; otherwise each step uses the Courant time step of its input state,
- * computed on the device (fused into the second stage of the previous step).
+/* Advance `nsteps` steps of the configured integrator.  dt_override > 0: every
+ * step uses that time step; otherwise each step uses the Courant time step of
+ * its input state, computed on the device (fused into the last kernel of the
+ * previous step).
  * t_out (may be NULL) receives the simulation time after the steps (problem 0
  * of a batch).  Returns after enqueueing when t_out is NULL and no error is
  * pending; otherwise synchronises and reports the device error word. */
@@ -133,7 +145,8 @@ dg_status dg_totals(dg_ctx* ctx, double* out);
 dg_status dg_divb(dg_ctx* ctx, double* out, int on_device);
 
 /* Vector-Jacobian product of one SSP-RK2 step with the time step held fixed
- * (the reverse of dg_step for gradients of an objective of the final state):
+ * (the reverse of dg_step for gradients of an objective of the final state;
+ * DG_SSPRK2 contexts only):
  *   lam_prev = (d U^{n+1} / d U^n)^T lam_next,   U^{n+1} = step(U^n; dt).
  * u_n, lam_next, lam_prev: device pointers, interchange layout, float64; lam_prev
  * may not alias the other two.  Euler, one problem, limiter off or on (the
@@ -183,7 +196,8 @@ dg_status dg_profile(dg_ctx* ctx, int enable);
 
 /* Totals of the recorded kernel times: ms[k] and launches[k] for k = 0 (stage 1)
  * and 1 (stage 2 incl. the fused time-step reduction).  A batch of 2D problems
- * runs both stages in one launch per step, counted under k = 1.  Synchronises. */
+ * runs both stages in one launch per step, and a MUSCL-Hancock step is one
+ * launch; both are counted under k = 1.  Synchronises. */
 dg_status dg_profile_read(dg_ctx* ctx, double ms[2], long long launches[2]);
 
 /* Name of the stage kernel and tile shape this context launches (chosen by the
@@ -193,8 +207,9 @@ const char* dg_kernel_name(const dg_ctx* ctx);
 
 /* Algorithmic DRAM bytes of one stage-kernel launch on the whole grid (all
  * problems): stage 1 reads and writes one state, stage 2 reads two and writes
- * one (a batch of 2D problems: 0 for stage 1, both stages for stage 2).  Used for
- * roofline figures. */
+ * one (a batch of 2D problems: 0 for stage 1, both stages for stage 2; a
+ * MUSCL-Hancock step: 0 for stage 1, one state read and one written for stage
+ * 2).  Used for roofline figures. */
 double dg_stage_bytes(const dg_ctx* ctx, int stage);
 
 #ifdef __cplusplus

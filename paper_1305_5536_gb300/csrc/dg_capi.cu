@@ -43,6 +43,7 @@ struct EvPair {
 struct dg_ctx {
   std::vector<Prob> probs;
   int eq = 0, dim = 2, fp32 = 0, limiter = 1, ckpt_every = 0;
+  int integrator = DG_SSPRK2, face_points = 2;  // face rule of the MUSCL-Hancock step
   double gamma = 1.4, cfl = 0.3;
   int nplanes = 0, nv = 0, ns = 0;
   PlaneMap pmap{};
@@ -125,6 +126,13 @@ const char* validate(const dg_config* c) {
   if (c->eq == DG_EULER && c->riemann != DG_EXACT) return "Euler uses the exact Riemann solver (DG_EXACT)";
   if (c->eq == DG_MHD && c->riemann != DG_HLLD) return "MHD uses the HLLD solver (DG_HLLD)";
   if (c->ckpt_every < 0) return "ckpt_every must be >= 0";
+  if (c->integrator != DG_SSPRK2 && c->integrator != DG_MUSCL_HANCOCK)
+    return "integrator must be DG_SSPRK2 or DG_MUSCL_HANCOCK";
+  if (c->face_points < 0 || c->face_points > 2) return "face_points must be 0, 1 or 2";
+  if (c->integrator == DG_SSPRK2 && c->face_points == 1)
+    return "the SSP-RK2 step uses the Gauss face rule (face_points 0 or 2)";
+  if (c->integrator == DG_MUSCL_HANCOCK && c->dim != 2)
+    return "the MUSCL-Hancock step is implemented in 2D";
   return nullptr;
 }
 
@@ -266,8 +274,32 @@ cudaError_t launch_stage(dg_ctx* c, int stage, int in, int base, int out, double
                  : launch_stage_t<double>(c, stage, in, base, out, dtov, lim);
 }
 
-// One SSP-RK2 step from buffer `a` into buffer `b` (buffer 1 holds V^1).
+// One MUSCL-Hancock step of every problem from buffer `a` into buffer `b`.
+template <class TS>
+cudaError_t launch_mh_t(dg_ctx* c, int a, int b, double dtov) {
+  for (size_t ip = 0; ip < c->probs.size(); ++ip) {
+    const Prob& p = c->probs[ip];
+    Stage2DArgs<TS> s;
+    s.nx = p.nx; s.ny = p.ny; s.ncell = p.ncell;
+    s.dx = p.dx; s.dy = p.dy;
+    s.gamma = c->gamma; s.cfl = c->cfl; s.dt_override = dtov; s.limiter = c->limiter;
+    s.gas.set(c->gamma);
+    s.in = sbuf<TS>(c, a, p);
+    s.base = s.in;
+    s.out = sbuf<TS>(c, b, p);
+    s.lim_sl = nullptr;
+    s.ctl = c->ctl + ip;
+    cudaError_t e = launch_mh2d(c->eq, c->variant < 0 ? 0 : c->variant, c->face_points, s,
+                                c->launch_stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// One step from buffer `a` into buffer `b` (SSP-RK2: buffer 1 holds V^1).
 cudaError_t launch_step(dg_ctx* c, int a, int b, double dtov) {
+  if (c->integrator == DG_MUSCL_HANCOCK)
+    return c->fp32 ? launch_mh_t<float>(c, a, b, dtov) : launch_mh_t<double>(c, a, b, dtov);
   if (c->batch2d)
     return c->fp32 ? launch_batch_step_t<float>(c, a, b, dtov) : launch_batch_step_t<double>(c, a, b, dtov);
   cudaError_t e = launch_stage(c, 1, a, a, 1, dtov, b);
@@ -276,7 +308,7 @@ cudaError_t launch_step(dg_ctx* c, int a, int b, double dtov) {
 }
 
 cudaError_t launch_step_profiled(dg_ctx* c, int a, int b, double dtov) {
-  if (c->batch2d) {
+  if (c->batch2d || c->integrator == DG_MUSCL_HANCOCK) {
     EvPair ev;
     ev.kind = 1;
     cudaEventCreate(&ev.a);
@@ -395,7 +427,9 @@ std::string tune_key(dg_ctx* c) {
   const Prob& p = c->probs[0];
   snprintf(b, sizeof(b), "eq%d_d%d_fp%d_lim%d_%dx%dx%d_np%zu", c->eq, c->dim, c->fp32 ? 32 : 64,
            c->limiter, p.nx, p.ny, p.nz, c->probs.size());
-  return b;
+  std::string k = b;
+  if (c->integrator == DG_MUSCL_HANCOCK) k += "_mh" + std::to_string(c->face_points);
+  return k;
 }
 
 void tune_load() {
@@ -435,8 +469,9 @@ dg_status autotune(dg_ctx* c) {
     c->variant = it->second;
     return DG_OK;
   }
-  int nvar = c->batch2d ? kBatchVariants
-                        : (c->dim == 2 ? stage2d_variants(c->eq, c->fp32) : stage3d_variants(c->fp32));
+  int nvar = c->integrator == DG_MUSCL_HANCOCK ? mh2d_variants(c->eq, c->fp32)
+             : c->batch2d ? kBatchVariants
+             : (c->dim == 2 ? stage2d_variants(c->eq, c->fp32) : stage3d_variants(c->fp32));
   if (nvar <= 1) {
     c->variant = 0;
     return DG_OK;
@@ -585,9 +620,11 @@ static dg_status init_common(const dg_config* cfgs, int nprob, void* stream, dg_
     const dg_config& a = cfgs[0];
     const dg_config& b = cfgs[i];
     if (b.eq != a.eq || b.dim != a.dim || b.precision != a.precision || b.gamma != a.gamma ||
-        b.cfl != a.cfl || b.limiter != a.limiter || b.riemann != a.riemann)
+        b.cfl != a.cfl || b.limiter != a.limiter || b.riemann != a.riemann ||
+        b.integrator != a.integrator || b.face_points != a.face_points)
       return fail(nullptr, DG_EINVAL,
-                  "batched problems must share eq, dim, precision, gamma, cfl, limiter, riemann");
+                  "batched problems must share eq, dim, precision, gamma, cfl, limiter, riemann, "
+                  "integrator, face_points");
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -598,6 +635,9 @@ static dg_status init_common(const dg_config* cfgs, int nprob, void* stream, dg_
   const dg_config& a = cfgs[0];
   c->eq = a.eq; c->dim = a.dim; c->fp32 = a.precision == DG_FP32; c->limiter = a.limiter;
   c->gamma = a.gamma; c->cfl = a.cfl; c->ckpt_every = a.ckpt_every;
+  c->integrator = a.integrator;
+  // MUSCL-Hancock: 0 or 1 = the face-centroid rule; SSP-RK2: always the Gauss rule
+  c->face_points = a.integrator == DG_MUSCL_HANCOCK && a.face_points != 2 ? 1 : 2;
   c->nplanes = nplanes_of(a.eq, a.dim);
   build_plane_map(c);
   c->stream = (cudaStream_t)stream;
@@ -624,7 +664,7 @@ static dg_status init_common(const dg_config* cfgs, int nprob, void* stream, dg_
     c->probs.push_back(p);
   }
   dg_status s = alloc_ctx(c);
-  if (s == DG_OK && nprob > 1 && c->dim == 2) s = build_batch(c);
+  if (s == DG_OK && nprob > 1 && c->dim == 2 && c->integrator == DG_SSPRK2) s = build_batch(c);
   if (s != DG_OK) {
     g_err = c->err;
     dg_destroy(c);
@@ -788,7 +828,7 @@ dg_status dg_profile_read(dg_ctx* c, double ms[2], long long launches[2]) {
     CK(c, cudaEventElapsedTime(&t, e.a, e.b));
     ms[e.kind] += t;
     // a batched 2D step is one launch; otherwise every problem is launched
-    launches[e.kind] += c->batch2d ? 1 : (long long)c->probs.size();
+    launches[e.kind] += c->batch2d && c->integrator == DG_SSPRK2 ? 1 : (long long)c->probs.size();
   }
   return DG_OK;
 }
@@ -799,7 +839,10 @@ const char* dg_kernel_name(const dg_ctx* cc) {
   const int v = c->variant < 0 ? 0 : c->variant;
   const char* prec = c->fp32 ? "fp32" : "fp64";
   char b[96];
-  if (c->batch2d)
+  if (c->integrator == DG_MUSCL_HANCOCK)
+    snprintf(b, sizeof(b), "mh2d_kernel %s %s %dpt", mh2d_variant_name(c->eq, c->fp32, v), prec,
+             c->face_points);
+  else if (c->batch2d)
     snprintf(b, sizeof(b), "batch2d_kernel %dx%d %s", batch2d_tile_x(c->fp32, v),
              batch2d_tile_y(c->fp32, v), prec);
   else if (c->dim == 2)
@@ -814,6 +857,8 @@ const char* dg_kernel_name(const dg_ctx* cc) {
 double dg_stage_bytes(const dg_ctx* c, int stage) {
   if (!c) return 0.0;
   double per = (double)c->nv * 8.0 + (double)c->ns * (c->fp32 ? 4.0 : 8.0);
+  if (c->integrator == DG_MUSCL_HANCOCK)  // one launch per step, reported as stage 2
+    return (stage == 1 ? 0.0 : 2.0) * per * (double)c->ncell_total;
   if (c->batch2d)  // one fused launch per step, reported as stage 2
     return (stage == 1 ? 0.0 : 5.0) * per * (double)c->ncell_total;
   return (stage == 1 ? 2.0 : 3.0) * per * (double)c->ncell_total;
@@ -825,6 +870,7 @@ double dg_stage_bytes(const dg_ctx* c, int stage) {
 dg_status dg_adjoint_step(dg_ctx* c, const double* lam_next, double* lam_prev, const double* u_n,
                           double dt) {
   if (!c || !lam_next || !lam_prev || !u_n) return fail(c, DG_EINVAL, "null argument");
+  if (c->integrator != DG_SSPRK2) return fail(c, DG_EINVAL, "the adjoint is that of the SSP-RK2 step");
   if (c->eq != DG_EULER || c->dim != 2 || c->probs.size() != 1)
     return fail(c, DG_EINVAL, "the adjoint is implemented for one 2D Euler problem");
   if (!(dt > 0.0)) return fail(c, DG_EINVAL, "dt must be > 0");
@@ -843,6 +889,7 @@ dg_status dg_record(dg_ctx* c, int nsteps, double dt_override, double* t_out) {
   if (!c) return DG_EINVAL;
   if (!c->state_set) return fail(c, DG_ESTATE, "no state has been set");
   if (c->ckpt_every < 1) return fail(c, DG_EINVAL, "recording needs cfg.ckpt_every >= 1");
+  if (c->integrator != DG_SSPRK2) return fail(c, DG_EINVAL, "the adjoint is that of the SSP-RK2 step");
   if (c->eq != DG_EULER || c->dim != 2 || c->probs.size() != 1)
     return fail(c, DG_EINVAL, "the adjoint is implemented for one 2D Euler problem");
   if (nsteps < 0) return fail(c, DG_EINVAL, "nsteps must be >= 0");

@@ -30,6 +30,14 @@ cudaError_t launch_stage2d(int eq, int variant, int stage, const Stage2DArgs<flo
 cudaError_t launch_stage3d(int variant, int stage, const Stage3DArgs<double>& a, cudaStream_t st);
 cudaError_t launch_stage3d(int variant, int stage, const Stage3DArgs<float>& a, cudaStream_t st);
 
+// MUSCL-Hancock step kernels (one launch per step; face_points 1 or 2).
+int mh2d_variants(int eq, int fp32);
+const char* mh2d_variant_name(int eq, int fp32, int v);
+cudaError_t launch_mh2d(int eq, int variant, int face_points, const Stage2DArgs<double>& a,
+                        cudaStream_t st);
+cudaError_t launch_mh2d(int eq, int variant, int face_points, const Stage2DArgs<float>& a,
+                        cudaStream_t st);
+
 // Layout conversion of one interchange plane (ncell doubles) to/from the state.
 template <class TS>
 cudaError_t launch_plane_in(const double* src, StateBuf<TS> dst, int kind, int idx, long ncell,

@@ -279,6 +279,69 @@ __device__ __forceinline__ void stage2d_load(const Stage2DArgs<TS>& A, const Til
   }
 }
 
+// End of a step on one tile: the Courant signal speed of the new averages o0[]
+// of this thread's cell, reduced over the grid (in TC; the CTA maximum is widened
+// to FP64 for the grid-wide atomic maximum); the last CTA of the grid to finish
+// publishes it for the next step and advances the time.  Also commits the error
+// word.
+template <int EQ, class TC, class TS, int NT>
+__device__ __forceinline__ void courant_commit2d(const Stage2DArgs<TS>& A, const Gas<TC>& G,
+                                                 bool owner, const double* o0, TC dx, TC dy,
+                                                 double dt, unsigned nblk, unsigned err,
+                                                 TileScalars<NT>& S) {
+  constexpr int NV = Tr2<EQ>::NV, NP = Tr2<EQ>::NP;
+  const int tid = threadIdx.x;
+  // Courant signal speed of the new state, reduced over the grid (in TC; the
+  // CTA maximum is widened to FP64 for the grid-wide atomic maximum)
+  TC sp = TC(0);
+  if (owner) {
+    TC c[NV], W[NP];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) c[v] = Cvt<TC>::to_tc(o0[v]);
+    prims2d<EQ, TC>(G, c, W, err);
+    TC cx, cy;
+    if (EQ == 0) {
+      cx = cy = sqrt(G.g * W[3] / W[0]);
+    } else {
+      TC b2 = W[4] * W[4] + W[5] * W[5];
+      cx = fast_speed(G, W[0], W[3], b2, W[4]);
+      cy = fast_speed(G, W[0], W[3], b2, W[5]);
+    }
+    sp = (fabs(W[1]) + cx) / dx + (fabs(W[2]) + cy) / dy;
+    if (!(sp >= TC(0))) { err |= ERR_NONPHYS; sp = TC(0); }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    TC t = __shfl_xor_sync(0xffffffffu, sp, o);
+    sp = t > sp ? t : sp;
+  }
+  if ((tid & 31) == 0) S.red[tid >> 5] = Cvt<TC>::to_f64(sp);
+  if (err) atomicOr(&S.err, err);
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < NT / 32; ++w) m = S.red[w] > m ? S.red[w] : m;
+    Ctl* ctl = A.ctl;
+    atomicMax(&ctl->vmax_next, (unsigned long long)__double_as_longlong(m));
+    if (S.err) atomicOr(&ctl->err, S.err);
+    __threadfence();
+    unsigned tk = atomicAdd(&ctl->ticket, 1u);
+    if (tk == nblk - 1) {
+      __threadfence();
+      double vm = __longlong_as_double((long long)atomicAdd(&ctl->vmax_next, 0ull));
+      ctl->vmax_cur = vm;
+      ctl->vmax_next = 0ull;
+      ctl->t += dt;
+      ctl->dt_last = dt;
+      if (ctl->dt_hist && ctl->step < ctl->hist_cap) ctl->dt_hist[ctl->step] = dt;
+      ctl->step += 1;
+      if (!(vm > 0.0)) ctl->err |= ERR_NONPHYS;
+      __threadfence();
+      ctl->ticket = 0u;
+    }
+  }
+}
+
 // The rest of a tile once it is staged: primitives, limiter, faces, per-cell
 // right-hand side and Runge-Kutta combination; `nblk` is the number of tiles of
 // the problem (the last of them to finish stage 2 publishes the Courant speed).
@@ -497,55 +560,7 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
   }
 
   if (STAGE == 2) {
-    // Courant signal speed of the new state, reduced over the grid (in TC; the
-    // CTA maximum is widened to FP64 for the grid-wide atomic maximum)
-    TC sp = TC(0);
-    if (owner) {
-      TC c[NV], W[NP];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) c[v] = Cvt<TC>::to_tc(o0[v]);
-      prims2d<EQ, TC>(G, c, W, err);
-      TC cx, cy;
-      if (EQ == 0) {
-        cx = cy = sqrt(G.g * W[3] / W[0]);
-      } else {
-        TC b2 = W[4] * W[4] + W[5] * W[5];
-        cx = fast_speed(G, W[0], W[3], b2, W[4]);
-        cy = fast_speed(G, W[0], W[3], b2, W[5]);
-      }
-      sp = (fabs(W[1]) + cx) / dx + (fabs(W[2]) + cy) / dy;
-      if (!(sp >= TC(0))) { err |= ERR_NONPHYS; sp = TC(0); }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      TC t = __shfl_xor_sync(0xffffffffu, sp, o);
-      sp = t > sp ? t : sp;
-    }
-    if ((tid & 31) == 0) S.red[tid >> 5] = Cvt<TC>::to_f64(sp);
-    if (err) atomicOr(&S.err, err);
-    __syncthreads();
-    if (tid == 0) {
-      double m = 0.0;
-      for (int w = 0; w < NT / 32; ++w) m = S.red[w] > m ? S.red[w] : m;
-      Ctl* ctl = A.ctl;
-      atomicMax(&ctl->vmax_next, (unsigned long long)__double_as_longlong(m));
-      if (S.err) atomicOr(&ctl->err, S.err);
-      __threadfence();
-      unsigned tk = atomicAdd(&ctl->ticket, 1u);
-      if (tk == nblk - 1) {
-        __threadfence();
-        double vm = __longlong_as_double((long long)atomicAdd(&ctl->vmax_next, 0ull));
-        ctl->vmax_cur = vm;
-        ctl->vmax_next = 0ull;
-        ctl->t += dt;
-        ctl->dt_last = dt;
-        if (ctl->dt_hist && ctl->step < ctl->hist_cap) ctl->dt_hist[ctl->step] = dt;
-        ctl->step += 1;
-        if (!(vm > 0.0)) ctl->err |= ERR_NONPHYS;
-        __threadfence();
-        ctl->ticket = 0u;
-      }
-    }
+    courant_commit2d<EQ, TC, TS, NT>(A, G, owner, o0, dx, dy, dt, nblk, err, S);
   } else {
     if (err) atomicOr(&S.err, err);
     __syncthreads();

@@ -21,6 +21,7 @@ DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONPHYS, DG_ETIMEOUT, DG_ESTATE = ran
 DG_EULER, DG_MHD = 0, 1
 DG_FP64, DG_FP32 = 0, 1
 DG_EXACT, DG_HLLD = 0, 1
+DG_SSPRK2, DG_MUSCL_HANCOCK = 0, 1
 _STATUS = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_ENONPHYS",
            5: "DG_ETIMEOUT", 6: "DG_ESTATE"}
 
@@ -42,7 +43,8 @@ class dg_config(ctypes.Structure):
                 ("box", ctypes.c_double * 3), ("gamma", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("limiter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("riemann", ctypes.c_int),
-                ("ckpt_every", ctypes.c_int)]
+                ("ckpt_every", ctypes.c_int), ("integrator", ctypes.c_int),
+                ("face_points", ctypes.c_int)]
 
 
 _lib = None
@@ -113,7 +115,9 @@ def _current_stream():
 
 
 def make_config(eq="euler", dim=2, n=(64, 64), box=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, cfl=0.3,
-                limiter=1, precision="fp64", ckpt_every=0):
+                limiter=1, precision="fp64", ckpt_every=0, integrator="rk2", face_points=0):
+    """integrator: "rk2" (two-stage SSP Runge-Kutta) or "mh" (MUSCL-Hancock, Sec. 2.4);
+    face_points: MUSCL-Hancock face rule, 1 (or 0) = face centroid, 2 = Gauss pair."""
     c = dg_config()
     c.eq = DG_MHD if eq in ("mhd", DG_MHD) else DG_EULER
     c.dim = dim
@@ -126,6 +130,8 @@ def make_config(eq="euler", dim=2, n=(64, 64), box=(1.0, 1.0, 1.0), gamma=5.0 / 
     c.precision = DG_FP32 if precision in ("fp32", DG_FP32) else DG_FP64
     c.riemann = DG_HLLD if c.eq == DG_MHD else DG_EXACT
     c.ckpt_every = int(ckpt_every)
+    c.integrator = DG_MUSCL_HANCOCK if integrator in ("mh", DG_MUSCL_HANCOCK) else DG_SSPRK2
+    c.face_points = int(face_points)
     return c
 
 
@@ -133,13 +139,15 @@ class DGSolver:
     """One periodic problem (or a batch of problems) stepped by the GPU library."""
 
     def __init__(self, eq="euler", dim=2, n=(64, 64), box=(1.0, 1.0, 1.0), gamma=5.0 / 3.0,
-                 cfl=0.3, limiter=1, precision="fp64", ckpt_every=0, stream=None, configs=None):
+                 cfl=0.3, limiter=1, precision="fp64", ckpt_every=0, stream=None, configs=None,
+                 integrator="rk2", face_points=0):
         L = load()
         self._L = L
         h = ctypes.c_void_p()
         st = _current_stream() if stream is None else ctypes.c_void_p(stream)
         if configs is None:
-            cfg = make_config(eq, dim, n, box, gamma, cfl, limiter, precision, ckpt_every)
+            cfg = make_config(eq, dim, n, box, gamma, cfl, limiter, precision, ckpt_every,
+                              integrator, face_points)
             self.configs = [cfg]
             s = L.dg_init(ctypes.byref(cfg), st, ctypes.byref(h))
         else:
