@@ -45,6 +45,12 @@ WORKLOADS = {
         "2D ideal MHD Orszag-Tang vortex 512x512, P1 DG, div-free B basis, HLLD, "
         "min/max limiter, CFL 0.3, MUSCL-Hancock step (Sec. 2.4) with one flux at each "
         "face centroid")),
+    "kh3d_256_mh": dict(eq="euler", dim=3, n=(256, 256, 256), integrator="mh", desc=(
+        "3D Euler Kelvin-Helmholtz shear layer 256^3, exact Riemann, limiter, CFL 0.3, "
+        "MUSCL-Hancock step (Sec. 2.4) with one flux at each face centroid")),
+    "kh3d_128_mh": dict(eq="euler", dim=3, n=(128, 128, 128), integrator="mh", desc=(
+        "3D Euler Kelvin-Helmholtz shear layer 128^3 (profiling size), exact Riemann, limiter, "
+        "CFL 0.3, MUSCL-Hancock step (Sec. 2.4) with one flux at each face centroid")),
     "mhd_batch64": dict(eq="mhd", dim=2, n=None, desc=(
         "64 independent 2D ideal-MHD problems, N log-uniform in [32, 512] (seeded), "
         "random-phase smooth v and div-free B, one persistent launch per step, CFL 0.3")),

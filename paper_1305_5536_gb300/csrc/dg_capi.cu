@@ -131,8 +131,6 @@ const char* validate(const dg_config* c) {
   if (c->face_points < 0 || c->face_points > 2) return "face_points must be 0, 1 or 2";
   if (c->integrator == DG_SSPRK2 && c->face_points == 1)
     return "the SSP-RK2 step uses the Gauss face rule (face_points 0 or 2)";
-  if (c->integrator == DG_MUSCL_HANCOCK && c->dim != 2)
-    return "the MUSCL-Hancock step is implemented in 2D";
   return nullptr;
 }
 
@@ -277,8 +275,24 @@ cudaError_t launch_stage(dg_ctx* c, int stage, int in, int base, int out, double
 // One MUSCL-Hancock step of every problem from buffer `a` into buffer `b`.
 template <class TS>
 cudaError_t launch_mh_t(dg_ctx* c, int a, int b, double dtov) {
+  const int v = c->variant < 0 ? 0 : c->variant;
   for (size_t ip = 0; ip < c->probs.size(); ++ip) {
     const Prob& p = c->probs[ip];
+    if (c->dim == 3) {
+      Stage3DArgs<TS> s;
+      s.nx = p.nx; s.ny = p.ny; s.nz = p.nz; s.ncell = p.ncell;
+      s.dx = p.dx; s.dy = p.dy; s.dz = p.dz;
+      s.gamma = c->gamma; s.cfl = c->cfl; s.dt_override = dtov; s.limiter = c->limiter;
+      s.gas.set(c->gamma);
+      s.in = sbuf<TS>(c, a, p);
+      s.base = s.in;
+      s.out = sbuf<TS>(c, b, p);
+      s.lim_sl = nullptr;
+      s.ctl = c->ctl + ip;
+      cudaError_t e = launch_mh3d(v, c->face_points, s, c->launch_stream);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     Stage2DArgs<TS> s;
     s.nx = p.nx; s.ny = p.ny; s.ncell = p.ncell;
     s.dx = p.dx; s.dy = p.dy;
@@ -289,8 +303,7 @@ cudaError_t launch_mh_t(dg_ctx* c, int a, int b, double dtov) {
     s.out = sbuf<TS>(c, b, p);
     s.lim_sl = nullptr;
     s.ctl = c->ctl + ip;
-    cudaError_t e = launch_mh2d(c->eq, c->variant < 0 ? 0 : c->variant, c->face_points, s,
-                                c->launch_stream);
+    cudaError_t e = launch_mh2d(c->eq, v, c->face_points, s, c->launch_stream);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -469,7 +482,8 @@ dg_status autotune(dg_ctx* c) {
     c->variant = it->second;
     return DG_OK;
   }
-  int nvar = c->integrator == DG_MUSCL_HANCOCK ? mh2d_variants(c->eq, c->fp32)
+  int nvar = c->integrator == DG_MUSCL_HANCOCK
+                 ? (c->dim == 2 ? mh2d_variants(c->eq, c->fp32) : mh3d_variants(c->fp32))
              : c->batch2d ? kBatchVariants
              : (c->dim == 2 ? stage2d_variants(c->eq, c->fp32) : stage3d_variants(c->fp32));
   if (nvar <= 1) {
@@ -839,8 +853,11 @@ const char* dg_kernel_name(const dg_ctx* cc) {
   const int v = c->variant < 0 ? 0 : c->variant;
   const char* prec = c->fp32 ? "fp32" : "fp64";
   char b[96];
-  if (c->integrator == DG_MUSCL_HANCOCK)
+  if (c->integrator == DG_MUSCL_HANCOCK && c->dim == 2)
     snprintf(b, sizeof(b), "mh2d_kernel %s %s %dpt", mh2d_variant_name(c->eq, c->fp32, v), prec,
+             c->face_points);
+  else if (c->integrator == DG_MUSCL_HANCOCK)
+    snprintf(b, sizeof(b), "mh3d_kernel %s %s %dpt", mh3d_variant_name(c->fp32, v), prec,
              c->face_points);
   else if (c->batch2d)
     snprintf(b, sizeof(b), "batch2d_kernel %dx%d %s", batch2d_tile_x(c->fp32, v),

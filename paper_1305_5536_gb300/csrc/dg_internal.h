@@ -37,6 +37,12 @@ cudaError_t launch_mh2d(int eq, int variant, int face_points, const Stage2DArgs<
                         cudaStream_t st);
 cudaError_t launch_mh2d(int eq, int variant, int face_points, const Stage2DArgs<float>& a,
                         cudaStream_t st);
+int mh3d_variants(int fp32);
+const char* mh3d_variant_name(int fp32, int v);
+cudaError_t launch_mh3d(int variant, int face_points, const Stage3DArgs<double>& a,
+                        cudaStream_t st);
+cudaError_t launch_mh3d(int variant, int face_points, const Stage3DArgs<float>& a,
+                        cudaStream_t st);
 
 // Layout conversion of one interchange plane (ncell doubles) to/from the state.
 template <class TS>

@@ -152,9 +152,56 @@ def test_mh_conservation_free_stream_and_batch(prec):
         assert err < TOL[prec], (m, err, where)
 
 
+def _kh_noisy(n, seed=5):
+    u = ics.kh3d(n, w0=0.1)
+    rng = np.random.default_rng(seed)
+    for v in range(5):
+        for k in range(1, 4):
+            u[v * 4 + k] += 0.02 * rng.standard_normal(u.shape[1:]) * (1 + abs(u[v * 4]))
+    return u
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("fp", [1, 2])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [(8, 8, 8), (12, 10, 6), (17, 9, 5), (1, 6, 4)])
+@pytest.mark.parametrize("limiter", [0, 1])
+def test_mh_euler3d_one_step(variant, fp, prec, n, limiter, monkeypatch):
+    monkeypatch.setenv("DG_TILE_VARIANT", str(variant))
+    u0 = _kh_noisy(n)
+    box = (1.0, 0.9, 1.1)
+    P = O.Problem(O.EULER, 3, n, box=box, limiter=limiter)
+    dt = 0.5 * P.cfl_dt(u0)[0]
+    ref, fl = P.mh_step(u0, dt, face_points=fp)
+    assert fl == 0
+    s = dg.DGSolver("euler", 3, n, box=box, limiter=limiter, precision=prec, integrator="mh",
+                    face_points=fp)
+    s.set_state(u0)
+    s.step(1, dt=dt, sync=True)
+    assert s.kernel_name().startswith("mh3d_kernel")
+    err, where = poly_rel_err(s.get_state(), ref, 0, 3, P.h)
+    s.close()
+    assert err < TOL[prec], (err, where)
+
+
+def test_mh_kh3d_64_courant_chain_fp64():
+    """KH shear layer 64^3, 6 steps with device Courant time steps, against the
+    oracle's run."""
+    n = (64, 64, 64)
+    u0 = ics.kh3d(n)
+    P = O.Problem(O.EULER, 3, n)
+    ref, dts, fl = P.mh_run(u0, 6, cfl=0.3)
+    assert fl == 0
+    s = dg.DGSolver("euler", 3, n, precision="fp64", integrator="mh")
+    s.set_state(u0)
+    t = s.step(6, sync=True)
+    assert abs(t - dts.sum()) < 1e-12 * dts.sum()
+    err, where = poly_rel_err(s.get_state(), ref, 0, 3, P.h)
+    s.close()
+    assert err < 1e-11, (err, where)
+
+
 def test_mh_rejects_what_it_does_not_implement():
-    with pytest.raises(dg.DGError):
-        dg.DGSolver("euler", 3, (8, 8, 8), integrator="mh")
     with pytest.raises(dg.DGError):
         dg.DGSolver("euler", 2, (8, 8), integrator="rk2", face_points=1)
     s = dg.DGSolver("euler", 2, (8, 8), integrator="mh", ckpt_every=2)
