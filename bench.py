@@ -81,13 +81,24 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _src_sha():
+# Sources each kernel family is compiled from (its ncu figures are void once any
+# of them changes).
+_FAMILY_SOURCES = {
+    "stage2d_kernel": ("dg_stage2d.cuh",),
+    "stage2d_tma_kernel": ("dg_stage2d.cuh", "dg_stage2d_tma.cuh", "dg_tma.cuh"),
+    "batch2d_kernel": ("dg_stage2d.cuh", "dg_batch.cu", "dg_batch.h"),
+    "stage3d_kernel": ("dg_stage3d.cuh",),
+    "mh2d_kernel": ("dg_stage2d.cuh", "dg_mh2d.cuh"),
+    "mh3d_kernel": ("dg_stage3d.cuh", "dg_mh3d.cuh"),
+}
+
+
+def _src_sha(kernel):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1305_5536_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.startswith("dg_stage") or f in ("dg_physics.cuh", "dg_common.cuh", "dg_tma.cuh",
-                                             "dg_batch.cu"):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    fam = _FAMILY_SOURCES.get(kernel.split()[0], ())
+    for f in sorted(fam + ("dg_physics.cuh", "dg_common.cuh")):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -100,7 +111,7 @@ def _traffic(kernel, workload):
     with open(p) as f:
         d = json.load(f)
     e = d.get(workload, {}).get(kernel)
-    if not e or e.get("src_sha") != _src_sha():
+    if not e or e.get("src_sha") != _src_sha(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
