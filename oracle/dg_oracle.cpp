@@ -10,7 +10,8 @@
 //                               `dgderiv3d`, mass matrix M, locally
 //                               divergence-free 2D magnetic basis V1..V5
 //   * Sec. 2.3                  exact Riemann solver (Euler), HLLD (MHD)
-//   * Sec. 2.5                  min/max slope limiter on primitive variables
+//   * Sec. 2.5                  min/max slope limiter on primitive variables, and
+//                               the WENO-type limiter (limiter = 2)
 //   * Sec. 2.6                  averaged normal B at faces; Stokes div-B estimate
 // The time integrator is the two-stage strong-stability-preserving Runge-Kutta
 // method (the "traditional DG" integrator named in Sec. 2.4) and faces are
@@ -106,7 +107,7 @@ struct Cfg {
   int eq;       // EQ_EULER | EQ_MHD
   int dim;      // 2 | 3 (MHD: 2 only)
   int nx, ny, nz;
-  int limiter;  // 0 off, 1 min/max limiter of Sec. 2.5
+  int limiter;  // 0 off, 1 min/max limiter, 2 WENO-type limiter (Sec. 2.5)
   int riemann;  // RS_EXACT | RS_HLLD
   int pad;
   double dx, dy, dz;
@@ -743,8 +744,8 @@ void limit_state(const Grid& G, const R* u, R* out, int& flags) {
     R dU[8][3], dW[8][3];
     conserved_gradients(G, u, c, dU);
     primitive_gradients(W, dU, g, dW);
-    // limiter coefficient of each primitive variable
-    auto alpha_of = [&](int q) {
+    // min/max limiter coefficient of primitive q for the gradient grad
+    auto alpha_of = [&](int q, const R* grad) {
       R phimax = W[q], phimin = W[q];
       for (int d = 0; d < dim; ++d)
         for (int s = -1; s <= 1; s += 2) {
@@ -756,7 +757,7 @@ void limit_state(const Grid& G, const R* u, R* out, int& flags) {
       for (int d = 0; d < dim; ++d)
         for (int s = -1; s <= 1; s += 2) {
           // Delta phi = grad phi . (face centroid - cell centroid)
-          R dphi = dW[q][d] * (0.5 * s * G.h[d]);
+          R dphi = grad[d] * (0.5 * s * G.h[d]);
           R psi(1.0);
           if (val(dphi) > 0.0) psi = (phimax - W[q]) / dphi;
           else if (val(dphi) < 0.0) psi = (phimin - W[q]) / dphi;
@@ -767,16 +768,76 @@ void limit_state(const Grid& G, const R* u, R* out, int& flags) {
     R dWl[8][3];
     for (int q = 0; q < 8; ++q) for (int d = 0; d < 3; ++d) dWl[q][d] = dW[q][d];
     int hydro_vars[5] = {0, 1, 2, 3, 4};
-    for (int h = 0; h < 5; ++h) {
-      int q = hydro_vars[h];
-      if (q == 3 && dim == 2) continue;  // vz carries no gradient in 2D
-      R a = alpha_of(q);
-      for (int d = 0; d < dim; ++d) dWl[q][d] = a * dW[q][d];
-    }
     R aB(1.0);
-    if (mhd) {
-      aB = r_min(alpha_of(5), alpha_of(6));
-      for (int d = 0; d < dim; ++d) { dWl[5][d] = aB * dW[5][d]; dWl[6][d] = aB * dW[6][d]; }
+    R aBk[3];  // the limited magnetic coefficients (a1, a2, a3)
+    if (G.c.limiter == 2) {
+      // Sec. 2.5, the WENO-type limiter.  Per primitive, two candidate gradients:
+      // the unlimited DG gradient and the stencil gradient of the FV method (the
+      // central difference of the face neighbours' centroid values, min/max
+      // limited); their weights are (eps + o_k)^(-1/2) with the oscillation factor
+      // o_k = sum_faces |Delta phi_f| + |phi_nbr - (phi + Delta phi_f)|.
+      const double eps = 2.220446049250313e-16;  // machine epsilon (double)
+      auto stencil = [&](int q, R gs[3]) {
+        for (int d = 0; d < 3; ++d) gs[d] = R(0.0);
+        for (int d = 0; d < dim; ++d)
+          gs[d] = (prim[(size_t)q * n + G.nbr(c, d, +1)] - prim[(size_t)q * n + G.nbr(c, d, -1)]) /
+                  (2.0 * G.h[d]);
+      };
+      auto osc = [&](int q, const R* gr) {
+        R o(0.0);
+        for (int d = 0; d < dim; ++d)
+          for (int s = -1; s <= 1; s += 2) {
+            R dphi = gr[d] * (0.5 * s * G.h[d]);
+            R pn = prim[(size_t)q * n + G.nbr(c, d, s)];
+            o = o + r_abs(dphi) + r_abs(pn - (W[q] + dphi));
+          }
+        return o;
+      };
+      for (int h = 0; h < 5; ++h) {
+        int q = hydro_vars[h];
+        if (q == 3 && dim == 2) continue;
+        R gs[3];
+        stencil(q, gs);
+        R a = alpha_of(q, gs);
+        for (int d = 0; d < dim; ++d) gs[d] = a * gs[d];
+        R wd = 1.0 / r_sqrt(eps + osc(q, dW[q]));
+        R ws = 1.0 / r_sqrt(eps + osc(q, gs));
+        for (int d = 0; d < dim; ++d) dWl[q][d] = (wd * dW[q][d] + ws * gs[d]) / (wd + ws);
+      }
+      if (mhd) {
+        // stencil gradients of Bx and By, each min/max limited as in the FV
+        // method, then projected in L2 over the cell onto the divergence-free
+        // basis: a1 = dBx/dy, a2 = dBy/dx, a3 = (dBx/dx dx^2 - dBy/dy dy^2)/(dx^2 + dy^2)
+        R gx[3], gy[3];
+        stencil(5, gx);
+        stencil(6, gy);
+        R ax = alpha_of(5, gx), ay = alpha_of(6, gy);
+        for (int d = 0; d < dim; ++d) { gx[d] = ax * gx[d]; gy[d] = ay * gy[d]; }
+        const double hx2 = G.h[0] * G.h[0], hy2 = G.h[1] * G.h[1];
+        R st[3] = {gx[1], gy[0], (gx[0] * hx2 - gy[1] * hy2) / (hx2 + hy2)};
+        R dg[3] = {u[(long)(b0 + 2) * n + c], u[(long)(b0 + 3) * n + c],
+                   u[(long)(b0 + 4) * n + c]};
+        // one weight pair for the field (oscillation factors of Bx and By added),
+        // so that the blend stays divergence free
+        R sbx[3] = {st[2], st[0], R(0.0)}, sby[3] = {st[1], -st[2], R(0.0)};
+        R wd = 1.0 / r_sqrt(eps + osc(5, dW[5]) + osc(6, dW[6]));
+        R ws = 1.0 / r_sqrt(eps + osc(5, sbx) + osc(6, sby));
+        for (int k = 0; k < 3; ++k) aBk[k] = (wd * dg[k] + ws * st[k]) / (wd + ws);
+        dWl[5][0] = aBk[2]; dWl[5][1] = aBk[0];
+        dWl[6][0] = aBk[1]; dWl[6][1] = -aBk[2];
+      }
+    } else {
+      for (int h = 0; h < 5; ++h) {
+        int q = hydro_vars[h];
+        if (q == 3 && dim == 2) continue;  // vz carries no gradient in 2D
+        R a = alpha_of(q, dW[q]);
+        for (int d = 0; d < dim; ++d) dWl[q][d] = a * dW[q][d];
+      }
+      if (mhd) {
+        aB = r_min(alpha_of(5, dW[5]), alpha_of(6, dW[6]));
+        for (int d = 0; d < dim; ++d) { dWl[5][d] = aB * dW[5][d]; dWl[6][d] = aB * dW[6][d]; }
+        for (int k = 0; k < 3; ++k) aBk[k] = aB * u[(long)(b0 + 2 + k) * n + c];
+      }
     }
     // back to conserved gradients by the product rule
     R dUl[8][3];
@@ -794,7 +855,7 @@ void limit_state(const Grid& G, const R* u, R* out, int& flags) {
     for (int v = 0; v < G.L.nT; ++v)
       for (int d = 0; d < dim; ++d) out[(long)(v * G.L.nK + 1 + d) * n + c] = dUl[G.L.tvar[v]][d];
     if (mhd)
-      for (int k = 2; k < 5; ++k) out[(long)(b0 + k) * n + c] = aB * u[(long)(b0 + k) * n + c];
+      for (int k = 0; k < 3; ++k) out[(long)(b0 + 2 + k) * n + c] = aBk[k];
   }
 }
 
