@@ -74,7 +74,9 @@ typedef struct {
   double box[3];    /* box lengths; cell size box[a]/n[a] */
   double gamma;     /* adiabatic index, > 1 */
   double cfl;       /* Courant number for the time step, > 0 */
-  int limiter;      /* 0 off, 1 min/max limiter of Sec. 2.5 */
+  int limiter;      /* 0 off, 1 min/max limiter of Sec. 2.5, 2 the WENO-type
+                       limiter of Sec. 2.5 (DG and min/max-limited stencil
+                       gradients weighted by their oscillation factors) */
   int precision;    /* DG_FP64 | DG_FP32 */
   int riemann;      /* DG_EXACT (Euler) | DG_HLLD (MHD); must match eq */
   int ckpt_every;   /* adjoint checkpoint stride k (>= 1); 0 = no recording */
@@ -149,7 +151,7 @@ dg_status dg_divb(dg_ctx* ctx, double* out, int on_device);
  * DG_SSPRK2 contexts only):
  *   lam_prev = (d U^{n+1} / d U^n)^T lam_next,   U^{n+1} = step(U^n; dt).
  * u_n, lam_next, lam_prev: device pointers, interchange layout, float64; lam_prev
- * may not alias the other two.  Euler, one problem, limiter off or on (the
+ * may not alias the other two.  Euler, one problem, limiter 0 or 1 (the
  * limiter contributes the derivative of its active branch).  The context's own
  * state is not changed.  Enqueued on the context stream. */
 dg_status dg_adjoint_step(dg_ctx* ctx, const double* lam_next, double* lam_prev,

@@ -121,7 +121,8 @@ const char* validate(const dg_config* c) {
   if (cells > 2.0e9) return "too many cells";
   if (!(c->gamma > 1.0) || !std::isfinite(c->gamma)) return "gamma must be > 1";
   if (!(c->cfl > 0.0) || !std::isfinite(c->cfl)) return "cfl must be > 0";
-  if (c->limiter != 0 && c->limiter != 1) return "limiter must be 0 or 1";
+  if (c->limiter < 0 || c->limiter > 2)
+    return "limiter must be 0 (off), 1 (min/max) or 2 (WENO-type)";
   if (c->precision != DG_FP64 && c->precision != DG_FP32) return "precision must be DG_FP64 or DG_FP32";
   if (c->eq == DG_EULER && c->riemann != DG_EXACT) return "Euler uses the exact Riemann solver (DG_EXACT)";
   if (c->eq == DG_MHD && c->riemann != DG_HLLD) return "MHD uses the HLLD solver (DG_HLLD)";
@@ -888,6 +889,8 @@ dg_status dg_adjoint_step(dg_ctx* c, const double* lam_next, double* lam_prev, c
                           double dt) {
   if (!c || !lam_next || !lam_prev || !u_n) return fail(c, DG_EINVAL, "null argument");
   if (c->integrator != DG_SSPRK2) return fail(c, DG_EINVAL, "the adjoint is that of the SSP-RK2 step");
+  if (c->limiter == 2)
+    return fail(c, DG_EINVAL, "the adjoint covers the min/max limiter (limiter 0 or 1)");
   if (c->eq != DG_EULER || c->dim != 2 || c->probs.size() != 1)
     return fail(c, DG_EINVAL, "the adjoint is implemented for one 2D Euler problem");
   if (!(dt > 0.0)) return fail(c, DG_EINVAL, "dt must be > 0");
@@ -907,6 +910,8 @@ dg_status dg_record(dg_ctx* c, int nsteps, double dt_override, double* t_out) {
   if (!c->state_set) return fail(c, DG_ESTATE, "no state has been set");
   if (c->ckpt_every < 1) return fail(c, DG_EINVAL, "recording needs cfg.ckpt_every >= 1");
   if (c->integrator != DG_SSPRK2) return fail(c, DG_EINVAL, "the adjoint is that of the SSP-RK2 step");
+  if (c->limiter == 2)
+    return fail(c, DG_EINVAL, "the adjoint covers the min/max limiter (limiter 0 or 1)");
   if (c->eq != DG_EULER || c->dim != 2 || c->probs.size() != 1)
     return fail(c, DG_EINVAL, "the adjoint is implemented for one 2D Euler problem");
   if (nsteps < 0) return fail(c, DG_EINVAL, "nsteps must be >= 0");

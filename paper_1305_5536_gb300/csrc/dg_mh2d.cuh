@@ -77,14 +77,20 @@ __device__ __forceinline__ MhMem2D<TC> mh2d_mem(unsigned char* base) {
 
 // Primitive gradients g[] of one cell (slot order of the derivative coefficients:
 // (rho, vx, vy, p) x (d/dx, d/dy), then a1, a2, a3) from its conserved
-// coefficients s[] at centroid primitives W; with `limit`, the min/max limiter
+// coefficients s[] at centroid primitives W; with limiter 1 the min/max limiter
 // (Sec. 2.5) scales them and s[] receives the limited conserved coefficients
-// (the same arithmetic as limit_cell2d).  Wn: the 4 face neighbours' primitives.
+// (the same arithmetic as limit_cell2d), with limiter 2 the WENO-type limiter
+// does (dg_weno.cuh).  Wn: the 4 face neighbours' primitives.
 template <int EQ, class TC>
 __device__ __forceinline__ void mh_grads2d(const Gas<TC>& G, const TC* hh, const TC* W,
-                                           const TC (*Wn)[Tr2<EQ>::NP], bool limit, TC* s,
+                                           const TC (*Wn)[Tr2<EQ>::NP], int limiter, TC* s,
                                            TC* g) {
   constexpr int NP = Tr2<EQ>::NP;
+  if (limiter == 2) {
+    weno_cell2d<EQ, TC>(G, hh, W, Wn, s, g);
+    return;
+  }
+  const bool limit = limiter != 0;
   const TC rho = W[0], vx = W[1], vy = W[2];
   const TC inv = TC(1) / rho;
   TC gr[2], gvx[2], gvy[2], gp[2], gbx[2], gby[2];
@@ -295,7 +301,7 @@ __device__ __forceinline__ void mh2d_compute(const Stage2DArgs<TS>& A, int i0, i
     }
 #pragma unroll
     for (int k = 0; k < NS; ++k) s[k] = s_sl[k * R1 + r1];
-    mh_grads2d<EQ, TC>(G, hh, W, Wn, A.limiter != 0, s, g);
+    mh_grads2d<EQ, TC>(G, hh, W, Wn, A.limiter, s, g);
     mh_rates2d<EQ, TC>(G, W, g, Wt);
 #pragma unroll
     for (int k = 0; k < NS; ++k) { s_sl[k * R1 + r1] = s[k]; s_g[k * R1 + r1] = g[k]; }

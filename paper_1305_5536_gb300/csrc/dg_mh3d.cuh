@@ -38,11 +38,20 @@ __host__ __device__ constexpr size_t mh3d_smem_bytes() {
 }
 
 // Primitive gradients g[v*3+d] (v = rho, vx, vy, vz, p) of one cell from its
-// conserved coefficients s[] at centroid primitives W; with `limit` the min/max
-// limiter scales them (Wn: the 6 face neighbours' primitives).
+// conserved coefficients s[] at centroid primitives W; limiter 1: the min/max
+// limiter scales them, 2: the WENO-type limiter (dg_weno.cuh) replaces them (Wn:
+// the 6 face neighbours' primitives).
 template <class TC>
 __device__ __forceinline__ void mh_grads3d(const Gas<TC>& G, const TC* hh, const TC* W,
-                                           const TC (*Wn)[5], bool limit, const TC* s, TC* g) {
+                                           const TC (*Wn)[5], int limiter, const TC* s, TC* g) {
+  if (limiter == 2) {
+    TC sc[15];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) sc[k] = s[k];
+    weno_cell3d<TC>(G, hh, W, Wn, sc, g);
+    return;
+  }
+  const bool limit = limiter != 0;
   const TC rho = W[0], inv = TC(1) / rho;
   const TC v[3] = {W[1], W[2], W[3]};
   const TC v2h = TC(0.5) * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
@@ -255,7 +264,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) mh3d_kernel(const Stage3DArgs<TS
     }
 #pragma unroll
     for (int k = 0; k < 15; ++k) s[k] = s_g[k * R1 + r1];
-    mh_grads3d<TC>(G, hh, W, Wn, A.limiter != 0, s, g);
+    mh_grads3d<TC>(G, hh, W, Wn, A.limiter, s, g);
     mh_rates3d<TC>(G, W, g, Wt);
 #pragma unroll
     for (int k = 0; k < 15; ++k) s_g[k * R1 + r1] = g[k];

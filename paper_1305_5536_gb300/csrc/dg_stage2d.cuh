@@ -30,6 +30,7 @@
 
 #include "dg_common.cuh"
 #include "dg_physics.cuh"
+#include "dg_weno.cuh"
 
 namespace dgk {
 
@@ -402,7 +403,8 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
       }
 #pragma unroll
       for (int k = 0; k < NS; ++k) s[k] = s_sl[k * R1 + r1];
-      limit_cell2d<EQ, TC>(G, hh, W, Wn, s);
+      if (A.limiter == 2) weno_cell2d<EQ, TC>(G, hh, W, Wn, s, nullptr);
+      else limit_cell2d<EQ, TC>(G, hh, W, Wn, s);
 #pragma unroll
       for (int k = 0; k < NS; ++k) s_sl[k * R1 + r1] = s[k];
     }
@@ -543,7 +545,8 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
         for (int v = 0; v < NV; ++v) c[v] = Cvt<TC>::to_tc(A.base.c0[v * ncell + nb[k]]);
         prims2d<EQ, TC>(G, c, Wn[k], err);
       }
-      limit_cell2d<EQ, TC>(G, hh, W, Wn, sn);
+      if (A.limiter == 2) weno_cell2d<EQ, TC>(G, hh, W, Wn, sn, nullptr);
+      else limit_cell2d<EQ, TC>(G, hh, W, Wn, sn);
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v)

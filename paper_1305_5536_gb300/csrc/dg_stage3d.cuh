@@ -21,6 +21,7 @@
 
 #include "dg_common.cuh"
 #include "dg_physics.cuh"
+#include "dg_weno.cuh"
 
 namespace dgk {
 
@@ -261,7 +262,8 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs
       }
 #pragma unroll
       for (int k = 0; k < 15; ++k) s[k] = s_sl[k * R1 + r1];
-      limit_cell3d<TC>(G, hh, W, Wn, s);
+      if (A.limiter == 2) weno_cell3d<TC>(G, hh, W, Wn, s, nullptr);
+      else limit_cell3d<TC>(G, hh, W, Wn, s);
 #pragma unroll
       for (int k = 0; k < 15; ++k) s_sl[k * R1 + r1] = s[k];
     }
@@ -394,7 +396,8 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs
         for (int v = 0; v < 5; ++v) c[v] = Cvt<TC>::to_tc(A.base.c0[v * ncell + nb[k]]);
         prims3d<TC>(G, c, Wn[k], err);
       }
-      limit_cell3d<TC>(G, hh, W, Wn, sn);
+      if (A.limiter == 2) weno_cell3d<TC>(G, hh, W, Wn, sn, nullptr);
+      else limit_cell3d<TC>(G, hh, W, Wn, sn);
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v)
