@@ -402,8 +402,9 @@ dg_status check_err(dg_ctx* c) {
     if (e)
       return fail(c, DG_ENONPHYS,
                   "problem %zu: device error word 0x%x (1 non-physical state, 2 Riemann vacuum, "
-                  "4 Newton iteration did not converge) at step %lld",
-                  p, e, (long long)c->ctl_host[p].step);
+                  "4 Newton iteration did not converge), first raised in step %lld (now after "
+                  "step %lld)",
+                  p, e, (long long)c->ctl_host[p].err_step, (long long)c->ctl_host[p].step);
   }
   return DG_OK;
 }

@@ -22,6 +22,7 @@ struct Ctl {
   unsigned int err;
   double* dt_hist;      // optional record of the time steps (adjoint)
   long long hist_cap;
+  long long err_step;   // step in which `err` was first raised (-1: never)
 };
 
 // One state: FP64 cell averages [nv][ncell] and derivative coefficients

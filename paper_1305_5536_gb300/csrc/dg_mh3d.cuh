@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) mh3d_kernel(const Stage3DArgs<TS
       ctl->t += dt;
       ctl->dt_last = dt;
       if (ctl->dt_hist && ctl->step < ctl->hist_cap) ctl->dt_hist[ctl->step] = dt;
+      if (ctl->err && ctl->err_step < 0) ctl->err_step = ctl->step;
       ctl->step += 1;
       if (!(vm > 0.0)) ctl->err |= ERR_NONPHYS;
       __threadfence();

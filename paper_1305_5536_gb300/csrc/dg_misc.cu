@@ -134,6 +134,7 @@ __global__ void ctl_reset_kernel(Ctl* ctl, int nprob) {
     ctl[p].step = 0;
     ctl[p].ticket = 0u;
     ctl[p].err = 0u;
+    ctl[p].err_step = -1;
   }
 }
 __global__ void ctl_commit_kernel(Ctl* ctl, int nprob) {
@@ -143,6 +144,7 @@ __global__ void ctl_commit_kernel(Ctl* ctl, int nprob) {
     ctl[p].vmax_cur = vm;
     ctl[p].vmax_next = 0ull;
     if (!(vm > 0.0)) ctl[p].err |= ERR_NONPHYS;
+    if (ctl[p].err && ctl[p].err_step < 0) ctl[p].err_step = ctl[p].step;
   }
 }
 cudaError_t launch_ctl_reset(Ctl* ctl, int nprob, cudaStream_t st) {

@@ -335,6 +335,7 @@ __device__ __forceinline__ void courant_commit2d(const Stage2DArgs<TS>& A, const
       ctl->t += dt;
       ctl->dt_last = dt;
       if (ctl->dt_hist && ctl->step < ctl->hist_cap) ctl->dt_hist[ctl->step] = dt;
+      if (ctl->err && ctl->err_step < 0) ctl->err_step = ctl->step;
       ctl->step += 1;
       if (!(vm > 0.0)) ctl->err |= ERR_NONPHYS;
       __threadfence();

@@ -270,3 +270,69 @@ def mhd_batch(nprob=64, nmin=32, nmax=512, seed=1305):
     sizes = batch_sizes(nprob, nmin, nmax, seed)
     rng = np.random.default_rng(seed + 1)
     return sizes, [mhd_random_smooth(N, rng=rng) for N in sizes]
+
+
+# ----------------------------------------------------------------------------
+# The paper's test problems (Sec. 3), analytic fields projected as above.
+# ----------------------------------------------------------------------------
+
+def gresho_fields(r):
+    """Sec. 3.3 triangle vortex: azimuthal velocity and pressure at radius r."""
+    vphi = np.where(r < 0.2, 5.0 * r, np.where(r < 0.4, 2.0 - 5.0 * r, 0.0))
+    rs = np.maximum(r, 1e-300)
+    p = np.where(r < 0.2, 5.0 + 12.5 * r * r,
+                 np.where(r < 0.4, 9.0 + 12.5 * r * r - 20.0 * r + 4.0 * np.log(rs / 0.2),
+                          3.0 + 4.0 * math.log(2.0)))
+    return vphi, p
+
+
+def gresho(n=(64, 64), gamma=5.0 / 3.0):
+    """Sec. 3.3 Gresho vortex: rho = 1, the steady triangle vortex centred in the
+    unit periodic box."""
+    def f(X, Y):
+        dx, dy = X - 0.5, Y - 0.5
+        r = np.sqrt(dx * dx + dy * dy)
+        vphi, p = gresho_fields(r)
+        rs = np.maximum(r, 1e-300)
+        return 1.0, -vphi * dy / rs, vphi * dx / rs, p
+    return project_2d(f, n, gamma=gamma)
+
+
+def implosion(n=(256, 256), gamma=1.4):
+    """Sec. 3.4 implosion: periodic box of side 0.3, gas at rest, (rho, p) = (1, 1)
+    for x + y > 0.15, else (0.125, 0.14)."""
+    def f(X, Y):
+        hi = X + Y > 0.15
+        return np.where(hi, 1.0, 0.125), 0.0, 0.0, np.where(hi, 1.0, 0.14)
+    return project_2d(f, n, box=(0.3, 0.3), gamma=gamma)
+
+
+def rotor(n=(512, 512), gamma=5.0 / 3.0, r0=0.1, r1=0.115):
+    """Sec. 3.7 magnetic rotor: p = 0.5, B = (2.5/sqrt(4 pi), 0), a dense disc
+    (rho = 10) spinning with angular velocity 1/r0 inside r0, tapered off to the
+    ambient gas at rest between r0 and r1 with f = (r1 - r)/(r1 - r0):
+    rho = 1 + 9 f, v = f v(r0) r0/r (continuous across both radii)."""
+    def f(X, Y):
+        dx, dy = X - 0.5, Y - 0.5
+        r = np.sqrt(dx * dx + dy * dy)
+        rs = np.maximum(r, 1e-300)
+        fr = (r1 - r) / (r1 - r0)
+        inner, taper = r <= r0, (r > r0) & (r <= r1)
+        rho = np.where(inner, 10.0, np.where(taper, 1.0 + 9.0 * fr, 1.0))
+        vx = np.where(inner, -dy / r0, np.where(taper, -fr * dy / rs, 0.0))
+        vy = np.where(inner, dx / r0, np.where(taper, fr * dx / rs, 0.0))
+        return rho, vx, vy, 0.5, 2.5 / math.sqrt(4.0 * math.pi), 0.0
+    return project_2d(f, n, gamma=gamma, eq=MHD)
+
+
+def sod_tube(N=64, L=20.0, gamma=1.4, left=(1.0, 1.0), right=(0.25, 0.1795)):
+    """Sec. 3.2 shock tube as a periodic 1D problem in 2D storage (one cell in y):
+    box [-L, L) with the left state (rho, p) on [-L, 0) and the right state on
+    [0, L), gas at rest; N cells per half.  Returns (u0, box)."""
+    nx = 2 * N
+    box = (2.0 * L, L / N)
+
+    def f(X, Y):
+        lft = X - L < 0
+        return (np.where(lft, left[0], right[0]), 0.0, 0.0, np.where(lft, left[1], right[1]))
+    return project_2d(f, (nx, 1), box=box, gamma=gamma), box
