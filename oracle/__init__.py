@@ -19,7 +19,7 @@ from . import build as _build
 
 EULER, MHD = 0, 1
 EXACT, HLLD = 0, 1
-FLAG_NONPHYS, FLAG_VACUUM, FLAG_NEWTON = 1, 2, 4
+FLAG_NONPHYS, FLAG_VACUUM, FLAG_NEWTON, FLAG_UNSUPPORTED = 1, 2, 4, 8
 
 
 class _Cfg(ctypes.Structure):
@@ -192,14 +192,17 @@ class Problem:
         return U
 
     def mass_matrices(self):
-        MT, MB = np.zeros(16), np.zeros(25)
+        """Taylor-basis and magnetic-basis mass matrices (the magnetic one 5x5 in
+        2D, 11x11 for 3D MHD)."""
+        MT, MB = np.zeros(16), np.zeros(121)
         lib().oracle_mass_matrices(ctypes.byref(self._c), _p(MT), _p(MB))
         k = self.dim + 1
-        return MT[: k * k].reshape(k, k), MB.reshape(5, 5)
+        nb = 11 if (self.eq == MHD and self.dim == 3) else 5
+        return MT[: k * k].reshape(k, k), MB[: nb * nb].reshape(nb, nb)
 
     def totals(self, u):
         u = self._chk(u)
-        nv = (4 if self.eq == MHD else (4 if self.dim == 2 else 5)) + (2 if self.eq == MHD else 0)
+        nv = (4 if self.dim == 2 else 5) + (self.dim if self.eq == MHD else 0)
         out = np.zeros(nv)
         lib().oracle_totals(ctypes.byref(self._c), _p(u), _p(out))
         return out

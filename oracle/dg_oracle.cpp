@@ -101,11 +101,12 @@ enum {
   FLAG_NONPHYS = 1,     // rho <= 0 or p <= 0 where a state is evaluated
   FLAG_VACUUM = 2,      // exact Riemann solver: vacuum generated
   FLAG_NEWTON = 4,      // exact Riemann solver: Newton iteration did not converge
+  FLAG_UNSUPPORTED = 8, // a combination the oracle does not define (WENO, 3D field)
 };
 
 struct Cfg {
   int eq;       // EQ_EULER | EQ_MHD
-  int dim;      // 2 | 3 (MHD: 2 only)
+  int dim;      // 2 | 3
   int nx, ny, nz;
   int limiter;  // 0 off, 1 min/max limiter, 2 WENO-type limiter (Sec. 2.5)
   int riemann;  // RS_EXACT | RS_HLLD
@@ -129,23 +130,25 @@ struct Layout {
   int nT;          // number of Taylor variables
   int tvar[5];     // U-index of each Taylor variable
   int nK;          // Taylor coefficients per variable = dim+1
-  int nB;          // magnetic coefficients (5 in 2D MHD, else 0)
+  int nB;          // magnetic coefficients (5 in 2D MHD, 11 in 3D MHD, else 0)
+  int nBa;         // of which averages (2 in 2D MHD, 3 in 3D MHD)
   int nplanes;
 };
 
 inline Layout layout_of(const Cfg& c) {
   Layout L;
   L.nK = c.dim + 1;
-  if (c.eq == EQ_MHD) {
+  L.nBa = 0;
+  if (c.dim == 2) {
     L.nT = 4; L.tvar[0] = I_RHO; L.tvar[1] = I_MX; L.tvar[2] = I_MY; L.tvar[3] = I_E;
-    L.nB = 5;
-  } else if (c.dim == 2) {
-    L.nT = 4; L.tvar[0] = I_RHO; L.tvar[1] = I_MX; L.tvar[2] = I_MY; L.tvar[3] = I_E;
-    L.nB = 0;
   } else {
     L.nT = 5; L.tvar[0] = I_RHO; L.tvar[1] = I_MX; L.tvar[2] = I_MY; L.tvar[3] = I_MZ;
     L.tvar[4] = I_E;
-    L.nB = 0;
+  }
+  L.nB = 0;
+  if (c.eq == EQ_MHD) {
+    L.nB = c.dim == 2 ? 5 : 11;
+    L.nBa = c.dim;
   }
   L.nplanes = L.nT * L.nK + L.nB;
   return L;
@@ -193,29 +196,47 @@ inline double gauss_weight(double h) { return 0.5 * h; }
 
 // ------------------------------------------------------------------------------
 // Basis functions (Sec. 2.2).  Local coordinates have their origin at the
-// centroid.  Scalar Taylor basis: W_0 = 1, W_k = x_k.  Vector magnetic basis
-// (2D, locally divergence free):
-//   V1 = (1,0), V2 = (0,1), V3 = (y,0), V4 = (0,x), V5 = (x,-y).
+// centroid.  Scalar Taylor basis: W_0 = 1, W_k = x_k.  Vector magnetic bases,
+// locally divergence free:
+//   2D: V1 = (1,0), V2 = (0,1), V3 = (y,0), V4 = (0,x), V5 = (x,-y);
+//   3D: V1..V3 the unit vectors, V4 = (y,0,0), V5 = (z,0,0), V6 = (0,x,0),
+//       V7 = (0,z,0), V8 = (0,0,x), V9 = (0,0,y), V10 = (x,-y,0), V11 = (x,0,-z).
 // ------------------------------------------------------------------------------
 inline double taylor_w(int k, const double x[3]) { return k == 0 ? 1.0 : x[k - 1]; }
 inline double taylor_dw(int k, int d) { return (k >= 1 && k - 1 == d) ? 1.0 : 0.0; }
-inline void mag_w(int k, const double x[3], double w[2]) {
+inline void mag_w(int dim, int k, const double x[3], double w[3]) {
+  w[0] = w[1] = w[2] = 0.0;
+  if (dim == 2) {
+    switch (k) {
+      case 0: w[0] = 1.0; break;
+      case 1: w[1] = 1.0; break;
+      case 2: w[0] = x[1]; break;
+      case 3: w[1] = x[0]; break;
+      default: w[0] = x[0]; w[1] = -x[1]; break;
+    }
+    return;
+  }
   switch (k) {
-    case 0: w[0] = 1.0; w[1] = 0.0; break;
-    case 1: w[0] = 0.0; w[1] = 1.0; break;
-    case 2: w[0] = x[1]; w[1] = 0.0; break;
-    case 3: w[0] = 0.0; w[1] = x[0]; break;
-    default: w[0] = x[0]; w[1] = -x[1]; break;
+    case 0: w[0] = 1.0; break;
+    case 1: w[1] = 1.0; break;
+    case 2: w[2] = 1.0; break;
+    case 3: w[0] = x[1]; break;
+    case 4: w[0] = x[2]; break;
+    case 5: w[1] = x[0]; break;
+    case 6: w[1] = x[2]; break;
+    case 7: w[2] = x[0]; break;
+    case 8: w[2] = x[1]; break;
+    case 9: w[0] = x[0]; w[1] = -x[1]; break;
+    default: w[0] = x[0]; w[2] = -x[2]; break;
   }
 }
 // d(component c of V_k)/d(x_d)
-inline double mag_dw(int k, int c, int d) {
-  switch (k) {
-    case 2: return (c == 0 && d == 1) ? 1.0 : 0.0;
-    case 3: return (c == 1 && d == 0) ? 1.0 : 0.0;
-    case 4: return (c == 0 && d == 0) ? 1.0 : ((c == 1 && d == 1) ? -1.0 : 0.0);
-    default: return 0.0;
-  }
+inline double mag_dw(int dim, int k, int c, int d) {
+  double x[3] = {0.0, 0.0, 0.0}, w0[3], w1[3];
+  mag_w(dim, k, x, w0);
+  x[d] = 1.0;
+  mag_w(dim, k, x, w1);
+  return w1[c] - w0[c];  // the basis is at most linear
 }
 
 // Value of the DG polynomial of cell `cell` at local point x: the 8-vector U.
@@ -231,12 +252,12 @@ void eval_poly(const Grid& G, const R* u, long cell, const double x[3], R U[8]) 
   }
   if (G.L.nB) {
     const int b0 = G.L.nT * G.L.nK;
-    for (int k = 0; k < 5; ++k) {
-      double w[2];
-      mag_w(k, x, w);
+    for (int k = 0; k < G.L.nB; ++k) {
+      double w[3];
+      mag_w(G.c.dim, k, x, w);
       R c = u[(long)(b0 + k) * n + cell];
-      U[I_BX] = U[I_BX] + c * w[0];
-      U[I_BY] = U[I_BY] + c * w[1];
+      for (int q = 0; q < 3; ++q)
+        if (w[q] != 0.0) U[I_BX + q] = U[I_BX + q] + c * w[q];
     }
   }
 }
@@ -681,7 +702,7 @@ int numerical_flux(const Cfg& c, const R UL[8], const R UR[8], int d, R F[8]) {
 // ------------------------------------------------------------------------------
 // Gradients dU[q][d] of the conserved variables of one cell's polynomial: its
 // Taylor derivative coefficients and, for MHD, the derivatives of the magnetic
-// basis expansion, dBx = (a3, a1), dBy = (a2, -a3).
+// basis expansion (2D: dBx = (a3, a1), dBy = (a2, -a3)).
 template <class R>
 void conserved_gradients(const Grid& G, const R* u, long c, R dU[8][3]) {
   const long n = G.ncell;
@@ -689,12 +710,12 @@ void conserved_gradients(const Grid& G, const R* u, long c, R dU[8][3]) {
   for (int q = 0; q < 8; ++q) for (int d = 0; d < 3; ++d) dU[q][d] = R(0.0);
   for (int v = 0; v < G.L.nT; ++v)
     for (int d = 0; d < G.c.dim; ++d) dU[G.L.tvar[v]][d] = u[(long)(v * G.L.nK + 1 + d) * n + c];
-  if (G.L.nB) {
-    R a1 = u[(long)(b0 + 2) * n + c], a2 = u[(long)(b0 + 3) * n + c],
-      a3 = u[(long)(b0 + 4) * n + c];
-    dU[I_BX][0] = a3; dU[I_BX][1] = a1;
-    dU[I_BY][0] = a2; dU[I_BY][1] = -a3;
-  }
+  for (int k = G.L.nBa; k < G.L.nB; ++k)
+    for (int q = 0; q < 3; ++q)
+      for (int d = 0; d < G.c.dim; ++d) {
+        const double w = mag_dw(G.c.dim, k, q, d);
+        if (w != 0.0) dU[I_BX + q][d] = dU[I_BX + q][d] + w * u[(long)(b0 + k) * n + c];
+      }
 }
 
 // Primitive gradients dW[q][d] at centroid primitives W by the product rule
@@ -769,8 +790,9 @@ void limit_state(const Grid& G, const R* u, R* out, int& flags) {
     for (int q = 0; q < 8; ++q) for (int d = 0; d < 3; ++d) dWl[q][d] = dW[q][d];
     int hydro_vars[5] = {0, 1, 2, 3, 4};
     R aB(1.0);
-    R aBk[3];  // the limited magnetic coefficients (a1, a2, a3)
-    if (G.c.limiter == 2) {
+    R aBk[8];  // the limited magnetic derivative coefficients
+    const int nBd = G.L.nB - G.L.nBa;
+    if (G.c.limiter == 2 && !(mhd && dim == 3)) {
       // Sec. 2.5, the WENO-type limiter.  Per primitive, two candidate gradients:
       // the unlimited DG gradient and the stencil gradient of the FV method (the
       // central difference of the face neighbours' centroid values, min/max
@@ -834,9 +856,13 @@ void limit_state(const Grid& G, const R* u, R* out, int& flags) {
         for (int d = 0; d < dim; ++d) dWl[q][d] = a * dW[q][d];
       }
       if (mhd) {
-        aB = r_min(alpha_of(5, dW[5]), alpha_of(6, dW[6]));
-        for (int d = 0; d < dim; ++d) { dWl[5][d] = aB * dW[5][d]; dWl[6][d] = aB * dW[6][d]; }
-        for (int k = 0; k < 3; ++k) aBk[k] = aB * u[(long)(b0 + 2 + k) * n + c];
+        // one factor for the whole field: min over its components (2D: Bx, By)
+        if (G.c.limiter == 2) flags |= FLAG_UNSUPPORTED;  // 3D field: min/max instead
+        aB = alpha_of(5, dW[5]);
+        for (int q = 1; q < G.L.nBa; ++q) aB = r_min(aB, alpha_of(5 + q, dW[5 + q]));
+        for (int q = 0; q < G.L.nBa; ++q)
+          for (int d = 0; d < dim; ++d) dWl[5 + q][d] = aB * dW[5 + q][d];
+        for (int k = 0; k < nBd; ++k) aBk[k] = aB * u[(long)(b0 + G.L.nBa + k) * n + c];
       }
     }
     // back to conserved gradients by the product rule
@@ -855,7 +881,7 @@ void limit_state(const Grid& G, const R* u, R* out, int& flags) {
     for (int v = 0; v < G.L.nT; ++v)
       for (int d = 0; d < dim; ++d) out[(long)(v * G.L.nK + 1 + d) * n + c] = dUl[G.L.tvar[v]][d];
     if (mhd)
-      for (int k = 0; k < 3; ++k) out[(long)(b0 + 2 + k) * n + c] = aBk[k];
+      for (int k = 0; k < nBd; ++k) out[(long)(b0 + G.L.nBa + k) * n + c] = aBk[k];
   }
 }
 
@@ -870,7 +896,7 @@ void limit_state(const Grid& G, const R* u, R* out, int& flags) {
 
 // Gaussian elimination with partial pivoting on a small dense system (double).
 static void invert_small(int m, const double* A, double* Ainv) {
-  double a[8][16];
+  double a[16][32];
   for (int i = 0; i < m; ++i)
     for (int j = 0; j < 2 * m; ++j) a[i][j] = j < m ? A[i * m + j] : (j - m == i ? 1.0 : 0.0);
   for (int col = 0; col < m; ++col) {
@@ -917,7 +943,7 @@ inline VolQuad vol_quad(const Grid& G) {
 // Mass matrices by quadrature (exact: the integrands are quadratic).
 struct Mass {
   double MT[4 * 4], MTinv[4 * 4];
-  double MB[5 * 5], MBinv[5 * 5];
+  double MB[11 * 11], MBinv[11 * 11];
 };
 inline Mass mass_matrices(const Grid& G) {
   Mass M;
@@ -930,18 +956,20 @@ inline Mass mass_matrices(const Grid& G) {
       M.MT[k * nK + l] = s;
     }
   invert_small(nK, M.MT, M.MTinv);
-  for (int k = 0; k < 5; ++k)
-    for (int l = 0; l < 5; ++l) {
+  const int nB = G.L.nB ? G.L.nB : 5;  // (the 2D basis when there is no field)
+  const int dimB = G.L.nB ? G.c.dim : 2;
+  for (int k = 0; k < nB; ++k)
+    for (int l = 0; l < nB; ++l) {
       double s = 0.0;
       for (int q = 0; q < Q.nq; ++q) {
-        double wk[2], wl[2];
-        mag_w(k, Q.x[q], wk);
-        mag_w(l, Q.x[q], wl);
-        s += Q.w[q] * (wk[0] * wl[0] + wk[1] * wl[1]);
+        double wk[3], wl[3];
+        mag_w(dimB, k, Q.x[q], wk);
+        mag_w(dimB, l, Q.x[q], wl);
+        s += Q.w[q] * (wk[0] * wl[0] + wk[1] * wl[1] + wk[2] * wl[2]);
       }
-      M.MB[k * 5 + l] = s;
+      M.MB[k * nB + l] = s;
     }
-  invert_small(5, M.MB, M.MBinv);
+  invert_small(nB, M.MB, M.MBinv);
   return M;
 }
 
@@ -1018,9 +1046,9 @@ void dg_rhs(const Grid& G, const R* u, R* rhs, int& flags) {
 
   // 2. per cell: assemble face and volume integrals for every basis function
   for (long c = 0; c < n; ++c) {
-    R bT[5][4], bB[5];
+    R bT[5][4], bB[11];
     for (int v = 0; v < 5; ++v) for (int k = 0; k < 4; ++k) bT[v][k] = R(0.0);
-    for (int k = 0; k < 5; ++k) bB[k] = R(0.0);
+    for (int k = 0; k < 11; ++k) bB[k] = R(0.0);
     // face terms: - int F_hat . n W dGamma
     for (int d = 0; d < dim; ++d)
       for (int s = -1; s <= 1; s += 2) {
@@ -1033,10 +1061,10 @@ void dg_rhs(const Grid& G, const R* u, R* rhs, int& flags) {
             for (int k = 0; k < nK; ++k)
               bT[v][k] = bT[v][k] - w * taylor_w(k, FQ.x[gp]) * F[G.L.tvar[v]];
           if (mhd)
-            for (int k = 0; k < 5; ++k) {
-              double wk[2];
-              mag_w(k, FQ.x[gp], wk);
-              bB[k] = bB[k] - w * (wk[0] * F[I_BX] + wk[1] * F[I_BY]);
+            for (int k = 0; k < G.L.nB; ++k) {
+              double wk[3];
+              mag_w(dim, k, FQ.x[gp], wk);
+              bB[k] = bB[k] - w * (wk[0] * F[I_BX] + wk[1] * F[I_BY] + wk[2] * F[I_BZ]);
             }
         }
       }
@@ -1053,8 +1081,10 @@ void dg_rhs(const Grid& G, const R* u, R* rhs, int& flags) {
           for (int k = 0; k < nK; ++k)
             bT[v][k] = bT[v][k] + VQ.w[q] * taylor_dw(k, d) * F[G.L.tvar[v]];
         if (mhd)
-          for (int k = 0; k < 5; ++k)
-            bB[k] = bB[k] + VQ.w[q] * (mag_dw(k, 0, d) * F[I_BX] + mag_dw(k, 1, d) * F[I_BY]);
+          for (int k = 0; k < G.L.nB; ++k)
+            bB[k] = bB[k] + VQ.w[q] * (mag_dw(dim, k, 0, d) * F[I_BX] +
+                                       mag_dw(dim, k, 1, d) * F[I_BY] +
+                                       mag_dw(dim, k, 2, d) * F[I_BZ]);
       }
     }
     // solve with the mass matrices
@@ -1065,9 +1095,9 @@ void dg_rhs(const Grid& G, const R* u, R* rhs, int& flags) {
         rhs[(long)(v * nK + k) * n + c] = s;
       }
     if (mhd)
-      for (int k = 0; k < 5; ++k) {
+      for (int k = 0; k < G.L.nB; ++k) {
         R s(0.0);
-        for (int l = 0; l < 5; ++l) s = s + M.MBinv[k * 5 + l] * bB[l];
+        for (int l = 0; l < G.L.nB; ++l) s = s + M.MBinv[k * G.L.nB + l] * bB[l];
         rhs[(long)(b0 + k) * n + c] = s;
       }
   }
@@ -1262,9 +1292,9 @@ int mh_step(const Grid& G, const double* vn, double* vout, double dt, int face_p
   // 3b, 4. per cell: face and volume integrals of every basis function, mass
   //        matrix solve, update of the limited coefficients
   for (long c = 0; c < n; ++c) {
-    double bT[5][4], bB[5];
+    double bT[5][4], bB[11];
     for (int v = 0; v < 5; ++v) for (int k = 0; k < 4; ++k) bT[v][k] = 0.0;
-    for (int k = 0; k < 5; ++k) bB[k] = 0.0;
+    for (int k = 0; k < 11; ++k) bB[k] = 0.0;
     for (int d = 0; d < dim; ++d)
       for (int s = -1; s <= 1; s += 2) {
         const FaceQuad& FQ = s > 0 ? FQp[d] : FQm[d];
@@ -1276,10 +1306,10 @@ int mh_step(const Grid& G, const double* vn, double* vout, double dt, int face_p
             for (int k = 0; k < nK; ++k)
               bT[v][k] -= w * taylor_w(k, FQ.x[gp]) * F[G.L.tvar[v]];
           if (mhd)
-            for (int k = 0; k < 5; ++k) {
-              double wk[2];
-              mag_w(k, FQ.x[gp], wk);
-              bB[k] -= w * (wk[0] * F[I_BX] + wk[1] * F[I_BY]);
+            for (int k = 0; k < G.L.nB; ++k) {
+              double wk[3];
+              mag_w(dim, k, FQ.x[gp], wk);
+              bB[k] -= w * (wk[0] * F[I_BX] + wk[1] * F[I_BY] + wk[2] * F[I_BZ]);
             }
         }
       }
@@ -1293,8 +1323,9 @@ int mh_step(const Grid& G, const double* vn, double* vout, double dt, int face_p
         for (int v = 0; v < nT; ++v)
           for (int k = 0; k < nK; ++k) bT[v][k] += VQ.w[q] * taylor_dw(k, d) * F[G.L.tvar[v]];
         if (mhd)
-          for (int k = 0; k < 5; ++k)
-            bB[k] += VQ.w[q] * (mag_dw(k, 0, d) * F[I_BX] + mag_dw(k, 1, d) * F[I_BY]);
+          for (int k = 0; k < G.L.nB; ++k)
+            bB[k] += VQ.w[q] * (mag_dw(dim, k, 0, d) * F[I_BX] + mag_dw(dim, k, 1, d) * F[I_BY] +
+                                mag_dw(dim, k, 2, d) * F[I_BZ]);
       }
     }
     for (int v = 0; v < nT; ++v)
@@ -1305,9 +1336,9 @@ int mh_step(const Grid& G, const double* vn, double* vout, double dt, int face_p
         vout[i] = un[i] + dt * s;
       }
     if (mhd)
-      for (int k = 0; k < 5; ++k) {
+      for (int k = 0; k < G.L.nB; ++k) {
         double s = 0.0;
-        for (int l = 0; l < 5; ++l) s += M.MBinv[k * 5 + l] * bB[l];
+        for (int l = 0; l < G.L.nB; ++l) s += M.MBinv[k * G.L.nB + l] * bB[l];
         const long i = (long)(b0 + k) * n + c;
         vout[i] = un[i] + dt * s;
       }
@@ -1482,10 +1513,10 @@ void oracle_mass_matrices(const Cfg* c, double* MT, double* MB) {
 }
 
 // Totals V * sum_cells(average) of every conserved variable (Taylor variables
-// then b1, b2), Neumaier-compensated.
+// then the field averages b1, b2[, b3]), Neumaier-compensated.
 void oracle_totals(const Cfg* c, const double* u, double* out) {
   Grid G(*c);
-  int nv = G.L.nT + (G.L.nB ? 2 : 0);
+  int nv = G.L.nT + G.L.nBa;
   for (int v = 0; v < nv; ++v) {
     int plane = v < G.L.nT ? v * G.L.nK : G.L.nT * G.L.nK + (v - G.L.nT);
     double s = 0.0, comp = 0.0;

@@ -336,3 +336,99 @@ def sod_tube(N=64, L=20.0, gamma=1.4, left=(1.0, 1.0), right=(0.25, 0.1795)):
         lft = X - L < 0
         return (np.where(lft, left[0], right[0]), 0.0, 0.0, np.where(lft, left[1], right[1]))
     return project_2d(f, (nx, 1), box=box, gamma=gamma), box
+
+
+# ----------------------------------------------------------------------------
+# 3D projection (Taylor variables and the 11-function divergence-free field
+# basis of Sec. 2.2), one z-layer of cells at a time.
+# ----------------------------------------------------------------------------
+
+def _proj_divfree_3d(B, l, W, h):
+    """Coefficients (b1, b2, b3, a4, ..., a11) of the 3D basis V1..V11 from the
+    field samples B[3][...,4,4,4] at local offsets l[3] with weights W (sum 1):
+    the basis is orthogonal on a Cartesian cell except V10 = (x,-y,0) and
+    V11 = (x,0,-z), whose 2x2 block [[hx^2+hy^2, hx^2], [hx^2, hx^2+hz^2]] / 12 is
+    solved explicitly."""
+    m = lambda f: np.einsum("...abc,abc->...", f, W)
+    hx2, hy2, hz2 = h[0] ** 2 / 12.0, h[1] ** 2 / 12.0, h[2] ** 2 / 12.0
+    b1, b2, b3 = m(B[0]), m(B[1]), m(B[2])
+    a4, a5 = m(B[0] * l[1]) / hy2, m(B[0] * l[2]) / hz2
+    a6, a7 = m(B[1] * l[0]) / hx2, m(B[1] * l[2]) / hz2
+    a8, a9 = m(B[2] * l[0]) / hx2, m(B[2] * l[1]) / hy2
+    r10 = m(B[0] * l[0] - B[1] * l[1])
+    r11 = m(B[0] * l[0] - B[2] * l[2])
+    det = (hx2 + hy2) * (hx2 + hz2) - hx2 * hx2
+    a10 = ((hx2 + hz2) * r10 - hx2 * r11) / det
+    a11 = ((hx2 + hy2) * r11 - hx2 * r10) / det
+    return b1, b2, b3, a4, a5, a6, a7, a8, a9, a10, a11
+
+
+def project_3d(prim_fn, n, box=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, eq=EULER):
+    """Project primitive fields onto the 3D bases.  ``prim_fn(X, Y, Z)`` returns
+    (rho, vx, vy, vz, p) for Euler, plus (Bx, By, Bz) for MHD."""
+    nx, ny, nz = n
+    h = (box[0] / nx, box[1] / ny, box[2] / nz)
+    npl = 20 + (11 if eq == MHD else 0)
+    u = np.zeros((npl, nz, ny, nx))
+    xc = (np.arange(nx) + 0.5) * h[0]
+    yc = (np.arange(ny) + 0.5) * h[1]
+    W = GW[:, None, None] * GW[None, :, None] * GW[None, None, :]  # [z, y, x]
+    lz = np.broadcast_to(h[2] * GX[:, None, None], (4, 4, 4))
+    ly = np.broadcast_to(h[1] * GX[None, :, None], (4, 4, 4))
+    lx = np.broadcast_to(h[0] * GX[None, None, :], (4, 4, 4))
+    X = xc[None, :, None, None, None] + lx[None, None]
+    Y = yc[:, None, None, None, None] + ly[None, None]
+    shp = (ny, nx, 4, 4, 4)
+    X, Y = np.broadcast_to(X, shp), np.broadcast_to(Y, shp)
+    for k in range(nz):
+        Z = np.broadcast_to((k + 0.5) * h[2] + lz, shp)
+        f = [np.broadcast_to(np.asarray(a, dtype=np.float64), shp) for a in prim_fn(X, Y, Z)]
+        rho, vx, vy, vz, p = f[:5]
+        b2 = 0.0
+        if eq == MHD:
+            b2 = f[5] ** 2 + f[6] ** 2 + f[7] ** 2
+        E = p / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz) + 0.5 * b2
+        for v, fld in enumerate((rho, rho * vx, rho * vy, rho * vz, E)):
+            u[4 * v, k] = np.einsum("ijabc,abc->ij", fld, W)
+            for d, (ll, hh) in enumerate(((lx, h[0]), (ly, h[1]), (lz, h[2]))):
+                u[4 * v + 1 + d, k] = np.einsum("ijabc,abc->ij", fld * ll, W) / (hh * hh / 12.0)
+        if eq == MHD:
+            co = _proj_divfree_3d(f[5:8], (lx, ly, lz), W, h)
+            for j, c in enumerate(co):
+                u[20 + j, k] = c
+    return u
+
+
+def alfven_cp_3d(n=(16, 16, 16), t=0.0, eps=0.1, rho=1.0, p=0.1, B0=1.0, gamma=5.0 / 3.0):
+    """Circularly polarised Alfven wave travelling along k = 2 pi (1, 1, 1) in the
+    unit periodic cube: B = B0 k^ + eps (e1 sin phi + e2 cos phi), v = -(B - B0 k^)
+    / sqrt(rho), rho and p uniform, phi = k.x - |k| B0/sqrt(rho) t: an exact
+    solution of ideal MHD of any amplitude."""
+    kh = np.array([1.0, 1.0, 1.0]) / math.sqrt(3.0)
+    e1 = np.array([1.0, -1.0, 0.0]) / math.sqrt(2.0)
+    e2 = np.cross(kh, e1)
+    vA = B0 / math.sqrt(rho)
+
+    def f(X, Y, Z):
+        ph = 2 * math.pi * ((X + Y + Z) - math.sqrt(3.0) * vA * t)
+        s, c = np.sin(ph), np.cos(ph)
+        dB = [eps * (e1[i] * s + e2[i] * c) for i in range(3)]
+        v = [-dB[i] / math.sqrt(rho) for i in range(3)]
+        B = [B0 * kh[i] + dB[i] for i in range(3)]
+        return (rho, v[0], v[1], v[2], p, B[0], B[1], B[2])
+    return project_3d(f, n, gamma=gamma, eq=MHD)
+
+
+def orszag_tang_3d(n=(128, 128, 128), gamma=5.0 / 3.0, eps=0.2):
+    """A 3D extension of the Orszag-Tang vortex: the 2D fields of Sec. 3.8 (B
+    scaled by 1/sqrt(4 pi)) with a z-modulated velocity, v = ((1 + eps sin 2 pi z)
+    (-sin 2 pi y), (1 + eps sin 2 pi z) sin 2 pi x, eps sin 2 pi z); B has no z
+    dependence and stays divergence free."""
+    s4 = 1.0 / math.sqrt(4 * math.pi)
+
+    def f(X, Y, Z):
+        m = 1 + eps * np.sin(2 * np.pi * Z)
+        return (gamma ** 2 / (4 * math.pi), -m * np.sin(2 * np.pi * Y), m * np.sin(2 * np.pi * X),
+                eps * np.sin(2 * np.pi * Z), gamma / (4 * math.pi), -s4 * np.sin(2 * np.pi * Y),
+                s4 * np.sin(4 * np.pi * X), 0.0)
+    return project_3d(f, n, gamma=gamma, eq=MHD)
