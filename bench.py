@@ -51,6 +51,9 @@ WORKLOADS = {
     "kh3d_128_mh": dict(eq="euler", dim=3, n=(128, 128, 128), integrator="mh", desc=(
         "3D Euler Kelvin-Helmholtz shear layer 128^3 (profiling size), exact Riemann, limiter, "
         "CFL 0.3, MUSCL-Hancock step (Sec. 2.4) with one flux at each face centroid")),
+    "ot3d_128": dict(eq="mhd", dim=3, n=(128, 128, 128), desc=(
+        "3D ideal MHD Orszag-Tang vortex with z-modulated velocity 128^3, P1 DG, 11-function "
+        "div-free B basis, HLLD, min/max limiter, CFL 0.3")),
     "mhd_batch64": dict(eq="mhd", dim=2, n=None, desc=(
         "64 independent 2D ideal-MHD problems, N log-uniform in [32, 512] (seeded), "
         "random-phase smooth v and div-free B, one persistent launch per step, CFL 0.3")),
@@ -63,7 +66,9 @@ def _workload_state(W):
     if W["n"] is None:
         sizes, us = ics.mhd_batch()
         return np.concatenate([u.ravel() for u in us]), sum(N * N for N in sizes), sizes
-    if W["eq"] == "mhd":
+    if W["eq"] == "mhd" and W["dim"] == 3:
+        u0 = ics.orszag_tang_3d(W["n"])
+    elif W["eq"] == "mhd":
         u0 = ics.orszag_tang(W["n"])
     elif W["dim"] == 3:
         u0 = ics.kh3d(W["n"])
@@ -88,6 +93,7 @@ _FAMILY_SOURCES = {
     "stage2d_tma_kernel": ("dg_stage2d.cuh", "dg_stage2d_tma.cuh", "dg_tma.cuh"),
     "batch2d_kernel": ("dg_stage2d.cuh", "dg_batch.cu", "dg_batch.h"),
     "stage3d_kernel": ("dg_stage3d.cuh",),
+    "stage3m_kernel": ("dg_stage3d.cuh", "dg_stage3m.cuh"),
     "mh2d_kernel": ("dg_stage2d.cuh", "dg_mh2d.cuh"),
     "mh3d_kernel": ("dg_stage3d.cuh", "dg_mh3d.cuh"),
 }

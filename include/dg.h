@@ -136,8 +136,10 @@ dg_status dg_sync(dg_ctx* ctx);
 dg_status dg_get_times(dg_ctx* ctx, double* t, double* dt_next);
 
 /* Totals V * sum_cells(average) of every conserved variable, FP64 with
- * compensated (Neumaier) summation: Taylor variables then, for MHD, b1 and b2.
- * `out` is a host array of (nvar * nprob) doubles.  Synchronises. */
+ * compensated (Neumaier) summation: Taylor variables then, for MHD, the field
+ * averages b1, b2 (2D) or b1, b2, b3 (3D).  `out` is a host array of
+ * (nvar * nprob) doubles, nvar = 4 (2D) or 5 (3D) Taylor variables + 0, 2 or 3
+ * field averages.  Synchronises. */
 dg_status dg_totals(dg_ctx* ctx, double* out);
 
 /* Sec. 2.6 Stokes estimate of div B per cell, (1/V) sum_faces B.n A with the
@@ -174,7 +176,7 @@ dg_status dg_adjoint(dg_ctx* ctx, const double* lam_N, double* lam_0);
  * allocate device memory (the paper has no counterpart: this is a service of the
  * library, not a step of the method).  Same result as dg_totals -- V * sum of the
  * cell averages of every conserved variable, FP64 with compensated summation,
- * Taylor variables then (MHD) b1, b2 -- but without a context and without any
+ * Taylor variables then (MHD) b1, b2[, b3] -- but without a context and without any
  * cudaMalloc/cudaFree: the per-block partial sums live in one fixed 512 KiB
  * static device array that every GPU loading the library keeps until exit.
  *   cfg: grid and equations of the state (precision, limiter and cfl unused).

@@ -105,14 +105,13 @@ dg_status fail(dg_ctx* c, dg_status s, const char* fmt, ...) {
 
 int nplanes_of(int eq, int dim) {
   int nT = (dim == 2) ? 4 : 5;
-  return nT * (dim + 1) + (eq == DG_MHD ? 5 : 0);
+  return nT * (dim + 1) + (eq == DG_MHD ? (dim == 2 ? 5 : 11) : 0);
 }
 
 const char* validate(const dg_config* c) {
   if (!c) return "null configuration";
   if (c->eq != DG_EULER && c->eq != DG_MHD) return "eq must be DG_EULER or DG_MHD";
   if (c->dim != 2 && c->dim != 3) return "dim must be 2 or 3";
-  if (c->eq == DG_MHD && c->dim != 2) return "MHD is implemented in 2D only";
   for (int a = 0; a < c->dim; ++a) {
     if (c->n[a] < 1 || c->n[a] > (1 << 20)) return "grid size out of range";
     if (!(c->box[a] > 0.0) || !std::isfinite(c->box[a])) return "box lengths must be positive";
@@ -129,6 +128,10 @@ const char* validate(const dg_config* c) {
   if (c->ckpt_every < 0) return "ckpt_every must be >= 0";
   if (c->integrator != DG_SSPRK2 && c->integrator != DG_MUSCL_HANCOCK)
     return "integrator must be DG_SSPRK2 or DG_MUSCL_HANCOCK";
+  if (c->eq == DG_MHD && c->dim == 3 && c->integrator != DG_SSPRK2)
+    return "3D MHD is stepped with the SSP-RK2 integrator";
+  if (c->eq == DG_MHD && c->dim == 3 && c->limiter == 2)
+    return "3D MHD takes limiter 0 or 1 (the WENO-type limiter covers 2D MHD and Euler)";
   if (c->face_points < 0 || c->face_points > 2) return "face_points must be 0, 1 or 2";
   if (c->integrator == DG_SSPRK2 && c->face_points == 1)
     return "the SSP-RK2 step uses the Gauss face rule (face_points 0 or 2)";
@@ -146,15 +149,18 @@ void build_plane_map(dg_ctx* c) {
       m.kind[p] = k == 0 ? 0 : 1;
       m.idx[p] = k == 0 ? v : v * c->dim + (k - 1);
     }
-  if (c->eq == DG_MHD) {  // b1, b2 averages 4, 5; a1, a2, a3 slopes 8, 9, 10
+  if (c->eq == DG_MHD && c->dim == 2) {  // b1, b2 averages 4, 5; a1, a2, a3 slopes 8, 9, 10
     m.kind[p] = 0; m.idx[p++] = 4;
     m.kind[p] = 0; m.idx[p++] = 5;
     m.kind[p] = 1; m.idx[p++] = 8;
     m.kind[p] = 1; m.idx[p++] = 9;
     m.kind[p] = 1; m.idx[p++] = 10;
+  } else if (c->eq == DG_MHD) {  // b1..b3 averages 5..7; a4..a11 slopes 15..22
+    for (int k = 0; k < 3; ++k) { m.kind[p] = 0; m.idx[p++] = 5 + k; }
+    for (int k = 0; k < 8; ++k) { m.kind[p] = 1; m.idx[p++] = 15 + k; }
   }
-  c->nv = nT + (c->eq == DG_MHD ? 2 : 0);
-  c->ns = nT * c->dim + (c->eq == DG_MHD ? 3 : 0);
+  c->nv = nT + (c->eq == DG_MHD ? c->dim : 0);
+  c->ns = nT * c->dim + (c->eq == DG_MHD ? (c->dim == 2 ? 3 : 8) : 0);
 }
 
 template <class TS>
@@ -259,7 +265,9 @@ cudaError_t launch_stage_t(dg_ctx* c, int stage, int in, int base, int out, doub
       a.out = sbuf<TS>(c, out, p);
       a.lim_sl = lim >= 0 ? sbuf<TS>(c, lim, p).sl : nullptr;
       a.ctl = c->ctl + ip;
-      cudaError_t e = launch_stage3d(c->variant < 0 ? 0 : c->variant, stage, a, c->launch_stream);
+      const int v = c->variant < 0 ? 0 : c->variant;
+      cudaError_t e = c->eq == DG_MHD ? launch_stage3m(v, stage, a, c->launch_stream)
+                                      : launch_stage3d(v, stage, a, c->launch_stream);
       if (e != cudaSuccess) return e;
     }
   }
@@ -487,7 +495,8 @@ dg_status autotune(dg_ctx* c) {
   int nvar = c->integrator == DG_MUSCL_HANCOCK
                  ? (c->dim == 2 ? mh2d_variants(c->eq, c->fp32) : mh3d_variants(c->fp32))
              : c->batch2d ? kBatchVariants
-             : (c->dim == 2 ? stage2d_variants(c->eq, c->fp32) : stage3d_variants(c->fp32));
+             : (c->dim == 2 ? stage2d_variants(c->eq, c->fp32)
+                : (c->eq == DG_MHD ? stage3m_variants(c->fp32) : stage3d_variants(c->fp32)));
   if (nvar <= 1) {
     c->variant = 0;
     return DG_OK;
@@ -809,6 +818,7 @@ dg_status dg_totals(dg_ctx* c, double* out) {
 dg_status dg_divb(dg_ctx* c, double* out, int on_device) {
   if (!c || !out) return fail(c, DG_EINVAL, "null argument");
   if (c->eq != DG_MHD) return fail(c, DG_EINVAL, "div B is defined for MHD only");
+  if (c->dim != 2) return fail(c, DG_EINVAL, "the Stokes div B estimate is implemented in 2D");
   if (!c->state_set) return fail(c, DG_ESTATE, "no state has been set");
   const Prob& p = c->probs[0];
   double* dst = on_device ? out : c->scratch;
@@ -867,6 +877,8 @@ const char* dg_kernel_name(const dg_ctx* cc) {
   else if (c->dim == 2)
     snprintf(b, sizeof(b), "%s %s %s", v >= 3 ? "stage2d_tma_kernel" : "stage2d_kernel",
              stage2d_variant_name(c->eq, c->fp32, v), prec);
+  else if (c->eq == DG_MHD)
+    snprintf(b, sizeof(b), "stage3m_kernel %s %s", stage3m_variant_name(c->fp32, v), prec);
   else
     snprintf(b, sizeof(b), "stage3d_kernel %s %s", stage3d_variant_name(c->fp32, v), prec);
   c->kname = b;

@@ -13,8 +13,8 @@ namespace dgk {
 // number idx[p] (kind 0) or derivative coefficient number idx[p] (kind 1).
 struct PlaneMap {
   int nplanes;
-  int kind[24];
-  int idx[24];
+  int kind[32];
+  int idx[32];
 };
 
 // Number of tile shapes compiled for each (equations, dimension, precision).
@@ -29,6 +29,11 @@ cudaError_t launch_stage2d(int eq, int variant, int stage, const Stage2DArgs<flo
                            cudaStream_t st);
 cudaError_t launch_stage3d(int variant, int stage, const Stage3DArgs<double>& a, cudaStream_t st);
 cudaError_t launch_stage3d(int variant, int stage, const Stage3DArgs<float>& a, cudaStream_t st);
+// 3D MHD (11-function field basis).
+int stage3m_variants(int fp32);
+const char* stage3m_variant_name(int fp32, int v);
+cudaError_t launch_stage3m(int variant, int stage, const Stage3DArgs<double>& a, cudaStream_t st);
+cudaError_t launch_stage3m(int variant, int stage, const Stage3DArgs<float>& a, cudaStream_t st);
 
 // MUSCL-Hancock step kernels (one launch per step; face_points 1 or 2).
 int mh2d_variants(int eq, int fp32);

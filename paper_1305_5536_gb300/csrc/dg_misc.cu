@@ -84,19 +84,22 @@ __global__ void cfl_kernel(int eq, int dim, StateBuf<TS> s, int nx, int ny, int 
                        (TC)s.c0[3 * ncell + i] * vz);
       ie = 4;
     }
-    TC bx = TC(0), by = TC(0), mag = TC(0);
+    TC bx = TC(0), by = TC(0), bz = TC(0), mag = TC(0);
     if (eq == 1) {
-      bx = (TC)s.c0[4 * ncell + i];
-      by = (TC)s.c0[5 * ncell + i];
-      mag = TC(0.5) * (bx * bx + by * by);
+      const int ib = ie + 1;  // the field averages follow the energy
+      bx = (TC)s.c0[ib * ncell + i];
+      by = (TC)s.c0[(ib + 1) * ncell + i];
+      if (dim == 3) bz = (TC)s.c0[(ib + 2) * ncell + i];
+      mag = TC(0.5) * (bx * bx + by * by + bz * bz);
     }
     TC p = G.gm1 * ((TC)s.c0[ie * ncell + i] - kin - mag);
     if (!(rho > TC(0) && p > TC(0))) { err |= ERR_NONPHYS; continue; }
     TC sp;
     if (eq == 1) {
-      TC b2 = bx * bx + by * by;
+      TC b2 = bx * bx + by * by + bz * bz;
       sp = (fabs(vx) + fast_speed(G, rho, p, b2, bx)) / (TC)dx +
            (fabs(vy) + fast_speed(G, rho, p, b2, by)) / (TC)dy;
+      if (dim == 3) sp += (fabs(vz) + fast_speed(G, rho, p, b2, bz)) / (TC)dz;
     } else {
       TC c = sqrt(G.g * p / rho);
       sp = (fabs(vx) + c) / (TC)dx + (fabs(vy) + c) / (TC)dy;

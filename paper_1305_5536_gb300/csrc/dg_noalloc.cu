@@ -113,7 +113,6 @@ extern "C" dg_status dg_totals_noalloc(const dg_config* cfg, const double* u, do
   if (!cfg || !u || !out) return fail(DG_EINVAL, "null argument");
   if (cfg->eq != DG_EULER && cfg->eq != DG_MHD) return fail(DG_EINVAL, "eq must be DG_EULER or DG_MHD");
   if (cfg->dim != 2 && cfg->dim != 3) return fail(DG_EINVAL, "dim must be 2 or 3");
-  if (cfg->eq == DG_MHD && cfg->dim != 2) return fail(DG_EINVAL, "MHD is 2D only");
   long ncell = 1;
   for (int a = 0; a < cfg->dim; ++a) {
     if (cfg->n[a] < 1) return fail(DG_EINVAL, "grid size must be >= 1");
@@ -134,6 +133,7 @@ extern "C" dg_status dg_totals_noalloc(const dg_config* cfg, const double* u, do
   if (cfg->eq == DG_MHD) {
     P.plane[P.nv++] = nT * K;
     P.plane[P.nv++] = nT * K + 1;
+    if (cfg->dim == 3) P.plane[P.nv++] = nT * K + 2;
   }
   double vol = 1.0;
   for (int a = 0; a < cfg->dim; ++a) vol *= cfg->box[a] / cfg->n[a];

@@ -6,7 +6,8 @@
 //   * the exact Riemann solver of the Euler equations (Sec. 2.3; Newton iteration
 //     on the pressure function with the adaptive PVRS/TRRS/TSRS first guess of
 //     Toro's textbook, sampled at x/t = 0),
-//   * the HLLD solver of Miyoshi & Kusano (2005) for planar ideal MHD (Sec. 2.3),
+//   * the HLLD solver of Miyoshi & Kusano (2005) for planar ideal MHD and with two
+//     transverse components for 3D MHD (Sec. 2.3),
 //   * the min/max slope limiter of one cell on primitive variables (Sec. 2.5).
 // Face solvers work in the face frame: normal velocity u, transverse velocities,
 // and return fluxes in that frame.
@@ -353,6 +354,123 @@ __device__ __forceinline__ void hlld_flux(const Gas<T>& G, T rL, T uL, T vL, T p
     T E2 = EsR + sqR * (vBsR - vBss) * sg;
     T U2[5] = {rsR, rsR * SM, rsR * vss, E2, btss};
     for (int q = 0; q < 5; ++q)
+      F[q] = FR[q] + SR * (UsR[q] - UR[q]) + SsR * (U2[q] - UsR[q]);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// HLLD solver with two transverse components (3D MHD): per side (rho, u, v, w, p,
+// bv, bw) with u normal and (v, w), (bv, bw) the transverse velocity and field;
+// bn the common normal field.  Output in the face frame: F[0] mass, F[1] normal
+// momentum, F[2], F[3] transverse momenta, F[4] energy, F[5], F[6] transverse
+// field fluxes (the normal-field flux is zero).  Same wave-speed estimates and
+// degeneracy switch as hlld_flux.
+// ----------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void hlld_flux3(const Gas<T>& G, T rL, T uL, T vL, T wL, T pL, T bvL,
+                                           T bwL, T rR, T uR, T vR, T wR, T pR, T bvR, T bwR,
+                                           T bn, T* F, unsigned& err) {
+  if (!(rL > T(0) && pL > T(0) && rR > T(0) && pR > T(0))) {
+    err |= ERR_NONPHYS;
+    for (int q = 0; q < 7; ++q) F[q] = T(0);
+    return;
+  }
+  const T bn2 = bn * bn;
+  const T b2L = bn2 + bvL * bvL + bwL * bwL, b2R = bn2 + bvR * bvR + bwR * bwR;
+  const T EL = pL * G.inv_gm1 + T(0.5) * rL * (uL * uL + vL * vL + wL * wL) + T(0.5) * b2L;
+  const T ER = pR * G.inv_gm1 + T(0.5) * rR * (uR * uR + vR * vR + wR * wR) + T(0.5) * b2R;
+  const T pTL = pL + T(0.5) * b2L, pTR = pR + T(0.5) * b2R;
+  const T cfL = fast_speed(G, rL, pL, b2L, bn), cfR = fast_speed(G, rR, pR, b2R, bn);
+  const T cmax = cfL > cfR ? cfL : cfR;
+  const T SL = (uL < uR ? uL : uR) - cmax;
+  const T SR = (uL < uR ? uR : uL) + cmax;
+  T FL[7], FR[7], UL[7], UR[7];
+  {
+    T vB = uL * bn + vL * bvL + wL * bwL;
+    FL[0] = rL * uL; FL[1] = rL * uL * uL + pTL - bn2; FL[2] = rL * uL * vL - bn * bvL;
+    FL[3] = rL * uL * wL - bn * bwL; FL[4] = (EL + pTL) * uL - bn * vB;
+    FL[5] = bvL * uL - vL * bn; FL[6] = bwL * uL - wL * bn;
+    UL[0] = rL; UL[1] = rL * uL; UL[2] = rL * vL; UL[3] = rL * wL; UL[4] = EL;
+    UL[5] = bvL; UL[6] = bwL;
+    vB = uR * bn + vR * bvR + wR * bwR;
+    FR[0] = rR * uR; FR[1] = rR * uR * uR + pTR - bn2; FR[2] = rR * uR * vR - bn * bvR;
+    FR[3] = rR * uR * wR - bn * bwR; FR[4] = (ER + pTR) * uR - bn * vB;
+    FR[5] = bvR * uR - vR * bn; FR[6] = bwR * uR - wR * bn;
+    UR[0] = rR; UR[1] = rR * uR; UR[2] = rR * vR; UR[3] = rR * wR; UR[4] = ER;
+    UR[5] = bvR; UR[6] = bwR;
+  }
+  if (SL > T(0)) {
+    for (int q = 0; q < 7; ++q) F[q] = FL[q];
+    return;
+  }
+  if (SR < T(0)) {
+    for (int q = 0; q < 7; ++q) F[q] = FR[q];
+    return;
+  }
+  const T dL = SL - uL, dR = SR - uR;
+  const T den = dR * rR - dL * rL;
+  const T SM = (dR * rR * uR - dL * rL * uL - pTR + pTL) / den;
+  const T pTs = (dR * rR * pTL - dL * rL * pTR + rL * rR * dR * dL * (uR - uL)) / den;
+  // single-star states
+  T rsL, vsL, wsL, bvsL, bwsL, EsL, rsR, vsR, wsR, bvsR, bwsR, EsR;
+  {
+    T dd = rL * dL * (SL - SM) - bn2;
+    rsL = rL * dL / (SL - SM);
+    if (fabs(dd) < Prec<T>::hlld_degenerate * (rL * dL * dL + bn2)) {
+      vsL = vL; wsL = wL; bvsL = bvL; bwsL = bwL;
+    } else {
+      T tv = bn * (SM - uL) / dd;
+      T tb = (rL * dL * dL - bn2) / dd;
+      vsL = vL - bvL * tv; wsL = wL - bwL * tv;
+      bvsL = bvL * tb; bwsL = bwL * tb;
+    }
+    T vB = uL * bn + vL * bvL + wL * bwL, vBs = SM * bn + vsL * bvsL + wsL * bwsL;
+    EsL = (dL * EL - pTL * uL + pTs * SM + bn * (vB - vBs)) / (SL - SM);
+    dd = rR * dR * (SR - SM) - bn2;
+    rsR = rR * dR / (SR - SM);
+    if (fabs(dd) < Prec<T>::hlld_degenerate * (rR * dR * dR + bn2)) {
+      vsR = vR; wsR = wR; bvsR = bvR; bwsR = bwR;
+    } else {
+      T tv = bn * (SM - uR) / dd;
+      T tb = (rR * dR * dR - bn2) / dd;
+      vsR = vR - bvR * tv; wsR = wR - bwR * tv;
+      bvsR = bvR * tb; bwsR = bwR * tb;
+    }
+    vB = uR * bn + vR * bvR + wR * bwR;
+    vBs = SM * bn + vsR * bvsR + wsR * bwsR;
+    EsR = (dR * ER - pTR * uR + pTs * SM + bn * (vB - vBs)) / (SR - SM);
+  }
+  T UsL[7] = {rsL, rsL * SM, rsL * vsL, rsL * wsL, EsL, bvsL, bwsL};
+  T UsR[7] = {rsR, rsR * SM, rsR * vsR, rsR * wsR, EsR, bvsR, bwsR};
+  const T sqL = rsqrtv(rsL), sqR = rsqrtv(rsR);
+  const T SsL = SM - fabs(bn) / sqL, SsR = SM + fabs(bn) / sqR;
+  if (SsL >= T(0)) {
+    for (int q = 0; q < 7; ++q) F[q] = FL[q] + SL * (UsL[q] - UL[q]);
+    return;
+  }
+  if (SsR <= T(0)) {
+    for (int q = 0; q < 7; ++q) F[q] = FR[q] + SR * (UsR[q] - UR[q]);
+    return;
+  }
+  // double-star states between the Alfven waves
+  const T sg = bn > T(0) ? T(1) : (bn < T(0) ? T(-1) : T(0));
+  const T inv = T(1) / (sqL + sqR);
+  const T vss = (sqL * vsL + sqR * vsR + (bvsR - bvsL) * sg) * inv;
+  const T wss = (sqL * wsL + sqR * wsR + (bwsR - bwsL) * sg) * inv;
+  const T bvss = (sqL * bvsR + sqR * bvsL + sqL * sqR * (vsR - vsL) * sg) * inv;
+  const T bwss = (sqL * bwsR + sqR * bwsL + sqL * sqR * (wsR - wsL) * sg) * inv;
+  const T vBss = SM * bn + vss * bvss + wss * bwss;
+  if (SM >= T(0)) {
+    T vBsL = SM * bn + vsL * bvsL + wsL * bwsL;
+    T E2 = EsL - sqL * (vBsL - vBss) * sg;
+    T U2[7] = {rsL, rsL * SM, rsL * vss, rsL * wss, E2, bvss, bwss};
+    for (int q = 0; q < 7; ++q)
+      F[q] = FL[q] + SL * (UsL[q] - UL[q]) + SsL * (U2[q] - UsL[q]);
+  } else {
+    T vBsR = SM * bn + vsR * bvsR + wsR * bwsR;
+    T E2 = EsR + sqR * (vBsR - vBss) * sg;
+    T U2[7] = {rsR, rsR * SM, rsR * vss, rsR * wss, E2, bvss, bwss};
+    for (int q = 0; q < 7; ++q)
       F[q] = FR[q] + SR * (UsR[q] - UR[q]) + SsR * (U2[q] - UsR[q]);
   }
 }

@@ -150,10 +150,10 @@ __device__ __forceinline__ void face_flux3d(const Gas<TC>& G, int d, const TC* c
   F[4] = Ff[4];
 }
 
-// Add the two faces of orientation D of a cell to its right-hand side; s_f holds
-// [var][face][gauss point] with the 2x2 points in the order (a, b) = (--, -+, +-, ++)
-// of the transverse axes (e1, e2).
-template <int D, class TC>
+// Add the two faces of orientation D of a cell to its right-hand side for NV
+// variables; s_f holds [var][face][gauss point] with the 2x2 points in the order
+// (a, b) = (--, -+, +-, ++) of the transverse axes (e1, e2).
+template <int D, class TC, int NV = 5>
 __device__ __forceinline__ void gather3d(const TC* s_f, int FMAX, int fm, int fp, const TC* hd,
                                          TC* rc0, TC* rs) {
   constexpr int E1 = D == 0 ? 1 : 0, E2 = D == 2 ? 1 : 2;
@@ -162,7 +162,7 @@ __device__ __forceinline__ void gather3d(const TC* s_f, int FMAX, int fm, int fp
   const TC ce1 = TC(0.86602540378443864676) / (hd[E1] * hd[D]);
   const TC ce2 = TC(0.86602540378443864676) / (hd[E2] * hd[D]);
 #pragma unroll
-  for (int v = 0; v < 5; ++v) {
+  for (int v = 0; v < NV; ++v) {
     const TC* m = s_f + (v * FMAX + fm) * 4;
     const TC* p = s_f + (v * FMAX + fp) * 4;
     TC Sm = (m[0] + m[1]) + (m[2] + m[3]), Sp = (p[0] + p[1]) + (p[2] + p[3]);

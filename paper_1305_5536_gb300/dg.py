@@ -114,6 +114,13 @@ def _current_stream():
     return ctypes.c_void_p(0)
 
 
+def num_totals(eq, dim):
+    """Number of conserved totals of a problem: the Taylor variables, then (MHD)
+    the field averages b1, b2[, b3]."""
+    mhd = eq in ("mhd", DG_MHD)
+    return (4 if dim == 2 else 5) + (dim if mhd else 0)
+
+
 def make_config(eq="euler", dim=2, n=(64, 64), box=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, cfl=0.3,
                 limiter=1, precision="fp64", ckpt_every=0, integrator="rk2", face_points=0):
     """integrator: "rk2" (two-stage SSP Runge-Kutta) or "mh" (MUSCL-Hancock, Sec. 2.4);
@@ -221,7 +228,7 @@ class DGSolver:
         return t, dt
 
     def totals(self):
-        nv = (4 if self.dim == 2 else 5) + (2 if self.eq == DG_MHD else 0)
+        nv = num_totals(self.eq, self.dim)
         out = np.zeros(nv * len(self.configs))
         self._check(self._L.dg_totals(self._h, out.ctypes.data_as(ctypes.c_void_p)))
         return out.reshape(len(self.configs), nv)
@@ -275,7 +282,7 @@ def totals_noalloc(u, eq="euler", dim=2, n=(64, 64), box=(1.0, 1.0, 1.0), stream
     interchange layout) without any device allocation by the library."""
     L = load()
     cfg = make_config(eq, dim, n, box)
-    nv = (4 if dim == 2 else 5) + (2 if cfg.eq == DG_MHD else 0)
+    nv = num_totals(cfg.eq, dim)
     out = np.zeros(nv)
     st = _current_stream() if stream is None else ctypes.c_void_p(stream)
     s = L.dg_totals_noalloc(ctypes.byref(cfg), ctypes.c_void_p(u.data_ptr()),

@@ -36,6 +36,21 @@ def poly_rel_err(got, ref, eq, dim, h):
         e = d.max() / (s if s > 0 else 1.0)
         if e > worst:
             worst, where = e, names[v]
+    if eq == 1 and dim == 3:
+        # Bx = b1 + (a10 + a11) x + a4 y + a5 z, By = b2 + a6 x - a10 y + a7 z,
+        # Bz = b3 + a8 x + a9 y - a11 z   (planes b1..b3, a4..a11 after the Taylor ones)
+        b0 = nT * K
+        dd = np.abs(got[b0:] - ref[b0:])
+        hx, hy, hz = 0.5 * h[0], 0.5 * h[1], 0.5 * h[2]
+        dbx = dd[0] + (dd[9] + dd[10]) * hx + dd[3] * hy + dd[4] * hz
+        dby = dd[1] + dd[5] * hx + dd[9] * hy + dd[6] * hz
+        dbz = dd[2] + dd[7] * hx + dd[8] * hy + dd[10] * hz
+        r = ref[b0:]
+        s = np.sqrt(r[0] ** 2 + r[1] ** 2 + r[2] ** 2).max()
+        e = max(dbx.max(), dby.max(), dbz.max()) / (s if s > 0 else 1.0)
+        if e > worst:
+            worst, where = e, "B"
+        return worst, where
     if eq == 1:
         b0 = nT * K
         g, r = got[b0:], ref[b0:]
