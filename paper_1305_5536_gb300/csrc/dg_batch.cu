@@ -98,7 +98,8 @@ __device__ __forceinline__ void sweep(const BatchArgs<TS>& B, unsigned char* sme
 }
 
 template <int EQ, class TC, class TS, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) batch2d_kernel(const BatchArgs<TS> B) {
+__global__ void __launch_bounds__(TX * TY, (StageMinBlocks<TX * TY, TC>::v))
+    batch2d_kernel(const BatchArgs<TS> B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   sweep<EQ, TC, TS, TX, TY, 1>(B, smem_raw);
   if (!grid_barrier(B.bar, gridDim.x + B.barrier_extra, B.spin_limit)) {

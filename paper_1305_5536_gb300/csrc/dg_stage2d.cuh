@@ -588,8 +588,17 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
   stage2d_compute<EQ, TC, TS, TX, TY, STAGE>(A, i0, j0, nblk, M, S);
 }
 
+// FP32: as many resident CTAs as 72 registers a thread allow (7 of 128 threads):
+// the stage kernels are latency bound.  FP64 keeps its registers (it would spill).
+template <int NT, class TC>
+struct StageMinBlocks {
+  static constexpr int v =
+      sizeof(TC) == 4 && 65536 / (72 * NT) > 0 ? 65536 / (72 * NT) : 1;
+};
+
 template <int EQ, class TC, class TS, int TX, int TY, int STAGE>
-__global__ void __launch_bounds__(TX * TY) stage2d_kernel(const Stage2DArgs<TS> A) {
+__global__ void __launch_bounds__(TX * TY, (StageMinBlocks<TX * TY, TC>::v))
+    stage2d_kernel(const Stage2DArgs<TS> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   stage2d_tile<EQ, TC, TS, TX, TY, STAGE>(A, blockIdx.x * TX, blockIdx.y * TY,
                                           gridDim.x * gridDim.y, smem_raw);

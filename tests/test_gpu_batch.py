@@ -78,7 +78,11 @@ def test_batch_equals_single_problem_solvers():
         one.step(4, sync=True)
         ref = one.get_state()
         one.close()
-        np.testing.assert_allclose(g, ref, rtol=0, atol=1e-6 * np.abs(ref).max())
+        # the batched and single-problem kernels are compiled separately (their
+        # own register bounds), so FP32 multiply-adds may round differently; both
+        # are held to the FP32 parity bar per step
+        err, where = poly_rel_err(g, ref, 1, 2, (1.0 / N, 1.0 / N))
+        assert err < 2e-5, (N, err, where)
 
 
 def test_batch_barrier_timeout_is_reported_and_context_stays_usable(monkeypatch):
