@@ -34,10 +34,18 @@ __host__ __device__ constexpr int stage3d_face_max() {
                                                           : TX * TY * (TZ + 1));
 }
 
+// The primitives of the halo-2 box [5][R2] are dead once the limiter has run;
+// the face fluxes [5][4][FMAX] then reuse their space.
+template <int TX, int TY, int TZ, class TC>
+__host__ __device__ constexpr size_t stage3d_wsz() {
+  return size_t(5) * (TX + 4) * (TY + 4) * (TZ + 4) > size_t(5) * 4 * stage3d_face_max<TX, TY, TZ, TC>()
+             ? size_t(5) * (TX + 4) * (TY + 4) * (TZ + 4)
+             : size_t(5) * 4 * stage3d_face_max<TX, TY, TZ, TC>();
+}
+
 template <int TX, int TY, int TZ, class TC>
 __host__ __device__ constexpr size_t stage3d_smem_bytes() {
-  return (size_t(5) * (TX + 4) * (TY + 4) * (TZ + 4) + size_t(20) * (TX + 2) * (TY + 2) * (TZ + 2) +
-          size_t(5) * 4 * stage3d_face_max<TX, TY, TZ, TC>()) * sizeof(TC) +
+  return (stage3d_wsz<TX, TY, TZ, TC>() + size_t(20) * (TX + 2) * (TY + 2) * (TZ + 2)) * sizeof(TC) +
          sizeof(int) * ((TX + 4) + (TY + 4) + (TZ + 4));
 }
 
@@ -175,8 +183,16 @@ __device__ __forceinline__ void gather3d(const TC* s_f, int FMAX, int fm, int fp
   }
 }
 
+// FP32: as many resident CTAs as 80 registers a thread allow (the kernel is
+// latency bound); FP64 keeps its registers.
+template <int NT, class TC>
+struct Stage3dMinBlocks {
+  static constexpr int v = sizeof(TC) == 4 && 65536 / (80 * NT) > 0 ? 65536 / (80 * NT) : 1;
+};
+
 template <class TC, class TS, int TX, int TY, int TZ, int STAGE>
-__global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs<TS> A) {
+__global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, TC>::v))
+    stage3d_kernel(const Stage3DArgs<TS> A) {
   constexpr int R2X = TX + 4, R2Y = TY + 4, R2Z = TZ + 4, R2 = R2X * R2Y * R2Z;
   constexpr int R1X = TX + 2, R1Y = TY + 2, R1Z = TZ + 2, R1 = R1X * R1Y * R1Z;
   constexpr int NT = TX * TY * TZ;
@@ -184,11 +200,12 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3d_kernel(const Stage3DArgs
   static_assert(NT % 32 == 0, "tile must be whole warps");
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TC* s_w = reinterpret_cast<TC*>(smem_raw);  // 5 x R2 primitives
-  TC* s_c0 = s_w + 5 * R2;                    // 5 x R1 averages
+  constexpr int WS = (int)stage3d_wsz<TX, TY, TZ, TC>();
+  TC* s_w = reinterpret_cast<TC*>(smem_raw);  // 5 x R2 primitives, then
+  TC* s_f = s_w;                              //   5 x 4 x FMAX face fluxes
+  TC* s_c0 = s_w + WS;                        // 5 x R1 averages
   TC* s_sl = s_c0 + 5 * R1;                   // 15 x R1 derivatives
-  TC* s_f = s_sl + 15 * R1;                   // 5 x 4 x FMAX face fluxes
-  int* s_gx = reinterpret_cast<int*>(s_f + 5 * 4 * FMAX);
+  int* s_gx = reinterpret_cast<int*>(s_sl + 15 * R1);
   int* s_gy = s_gx + R2X;
   int* s_gz = s_gy + R2Y;
   __shared__ double s_dt;
