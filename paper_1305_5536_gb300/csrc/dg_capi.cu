@@ -479,24 +479,28 @@ void tune_save() {
 
 dg_status autotune(dg_ctx* c) {
   if (c->variant >= 0) return DG_OK;
-  // an explicit choice (DG_TILE_VARIANT) wins over the tuning cache
-  const char* env = getenv("DG_TILE_VARIANT");
-  if (env) {
-    c->variant = atoi(env);
-    return DG_OK;
-  }
-  tune_load();
-  std::string key = tune_key(c);
-  auto it = g_tune.find(key);
-  if (it != g_tune.end()) {
-    c->variant = it->second;
-    return DG_OK;
-  }
   int nvar = c->integrator == DG_MUSCL_HANCOCK
                  ? (c->dim == 2 ? mh2d_variants(c->eq, c->fp32) : mh3d_variants(c->fp32))
              : c->batch2d ? kBatchVariants
              : (c->dim == 2 ? stage2d_variants(c->eq, c->fp32)
                 : (c->eq == DG_MHD ? stage3m_variants(c->fp32) : stage3d_variants(c->fp32)));
+  // an explicit choice (DG_TILE_VARIANT) wins over the tuning cache when this
+  // kind of context has that tile shape
+  const char* env = getenv("DG_TILE_VARIANT");
+  if (env) {
+    const int v = atoi(env);
+    if (v >= 0 && v < nvar) {
+      c->variant = v;
+      return DG_OK;
+    }
+  }
+  tune_load();
+  std::string key = tune_key(c);
+  auto it = g_tune.find(key);
+  if (it != g_tune.end() && it->second >= 0 && it->second < nvar) {
+    c->variant = it->second;
+    return DG_OK;
+  }
   if (nvar <= 1) {
     c->variant = 0;
     return DG_OK;

@@ -31,10 +31,18 @@
 
 namespace dgk {
 
+// The primitives of the halo-2 box [8][R2] are dead once the limiter has run;
+// the face fluxes [8][4][FMAX] then reuse their space.
+template <int TX, int TY, int TZ, class TC>
+__host__ __device__ constexpr size_t stage3m_wsz() {
+  return size_t(8) * (TX + 4) * (TY + 4) * (TZ + 4) > size_t(8) * 4 * stage3d_face_max<TX, TY, TZ, TC>()
+             ? size_t(8) * (TX + 4) * (TY + 4) * (TZ + 4)
+             : size_t(8) * 4 * stage3d_face_max<TX, TY, TZ, TC>();
+}
+
 template <int TX, int TY, int TZ, class TC>
 __host__ __device__ constexpr size_t stage3m_smem_bytes() {
-  return (size_t(8) * (TX + 4) * (TY + 4) * (TZ + 4) + size_t(31) * (TX + 2) * (TY + 2) * (TZ + 2) +
-          size_t(8) * 4 * stage3d_face_max<TX, TY, TZ, TC>()) * sizeof(TC) +
+  return (stage3m_wsz<TX, TY, TZ, TC>() + size_t(31) * (TX + 2) * (TY + 2) * (TZ + 2)) * sizeof(TC) +
          sizeof(int) * ((TX + 4) + (TY + 4) + (TZ + 4));
 }
 
@@ -212,11 +220,12 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3m_kernel(const Stage3DArgs
   (void)R1Z;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TC* s_w = reinterpret_cast<TC*>(smem_raw);  // 8 x R2 primitives
-  TC* s_c0 = s_w + 8 * R2;                    // 8 x R1 averages
+  constexpr int WS = (int)stage3m_wsz<TX, TY, TZ, TC>();
+  TC* s_w = reinterpret_cast<TC*>(smem_raw);  // 8 x R2 primitives, then
+  TC* s_f = s_w;                              //   8 x 4 x FMAX face fluxes
+  TC* s_c0 = s_w + WS;                        // 8 x R1 averages
   TC* s_sl = s_c0 + 8 * R1;                   // 23 x R1 derivative coefficients
-  TC* s_f = s_sl + 23 * R1;                   // 8 x 4 x FMAX face fluxes
-  int* s_gx = reinterpret_cast<int*>(s_f + 8 * 4 * FMAX);
+  int* s_gx = reinterpret_cast<int*>(s_sl + 23 * R1);
   int* s_gy = s_gx + R2X;
   int* s_gz = s_gy + R2Y;
   __shared__ double s_dt;
