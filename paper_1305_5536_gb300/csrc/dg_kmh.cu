@@ -6,26 +6,30 @@
 
 namespace dgk {
 
-template <int EQ, class TC, class TS, int TX, int TY, int NGF>
+template <int EQ, class TC, class TS, int TX, int TY, int NGF, bool WENO>
 static cudaError_t launch_mh2d_t(const Stage2DArgs<TS>& a, cudaStream_t st) {
   constexpr size_t smem = mh2d_smem_bytes<EQ, TX, TY, NGF, TC>();
   static_assert(smem <= 227 * 1024, "tile too large for shared memory");
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(mh2d_kernel<EQ, TC, TS, TX, TY, NGF>,
+    cudaError_t e = cudaFuncSetAttribute(mh2d_kernel<EQ, TC, TS, TX, TY, NGF, WENO>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
-  mh2d_kernel<EQ, TC, TS, TX, TY, NGF><<<grid, TX * TY, smem, st>>>(a);
+  mh2d_kernel<EQ, TC, TS, TX, TY, NGF, WENO><<<grid, TX * TY, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <int EQ, class TC, class TS, int TX, int TY>
 static cudaError_t launch_mh2d_ngf(int face_points, const Stage2DArgs<TS>& a, cudaStream_t st) {
-  if (face_points == 2) return launch_mh2d_t<EQ, TC, TS, TX, TY, 2>(a, st);
-  return launch_mh2d_t<EQ, TC, TS, TX, TY, 1>(a, st);
+  if (a.limiter == 2) {
+    if (face_points == 2) return launch_mh2d_t<EQ, TC, TS, TX, TY, 2, true>(a, st);
+    return launch_mh2d_t<EQ, TC, TS, TX, TY, 1, true>(a, st);
+  }
+  if (face_points == 2) return launch_mh2d_t<EQ, TC, TS, TX, TY, 2, false>(a, st);
+  return launch_mh2d_t<EQ, TC, TS, TX, TY, 1, false>(a, st);
 }
 
 int mh2d_variants(int, int) { return 3; }

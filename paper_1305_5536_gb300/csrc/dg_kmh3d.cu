@@ -6,26 +6,30 @@
 
 namespace dgk {
 
-template <class TC, class TS, int TX, int TY, int TZ, int NGF>
+template <class TC, class TS, int TX, int TY, int TZ, int NGF, bool WENO>
 static cudaError_t launch_mh3d_t(const Stage3DArgs<TS>& a, cudaStream_t st) {
   constexpr size_t smem = mh3d_smem_bytes<TX, TY, TZ, NGF, TC>();
   static_assert(smem <= 227 * 1024, "tile too large for shared memory");
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(mh3d_kernel<TC, TS, TX, TY, TZ, NGF>,
+    cudaError_t e = cudaFuncSetAttribute(mh3d_kernel<TC, TS, TX, TY, TZ, NGF, WENO>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + TZ - 1) / TZ);
-  mh3d_kernel<TC, TS, TX, TY, TZ, NGF><<<grid, TX * TY * TZ, smem, st>>>(a);
+  mh3d_kernel<TC, TS, TX, TY, TZ, NGF, WENO><<<grid, TX * TY * TZ, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <class TC, class TS, int TX, int TY, int TZ>
 static cudaError_t launch_mh3d_ngf(int face_points, const Stage3DArgs<TS>& a, cudaStream_t st) {
-  if (face_points == 2) return launch_mh3d_t<TC, TS, TX, TY, TZ, 2>(a, st);
-  return launch_mh3d_t<TC, TS, TX, TY, TZ, 1>(a, st);
+  if (a.limiter == 2) {
+    if (face_points == 2) return launch_mh3d_t<TC, TS, TX, TY, TZ, 2, true>(a, st);
+    return launch_mh3d_t<TC, TS, TX, TY, TZ, 1, true>(a, st);
+  }
+  if (face_points == 2) return launch_mh3d_t<TC, TS, TX, TY, TZ, 2, false>(a, st);
+  return launch_mh3d_t<TC, TS, TX, TY, TZ, 1, false>(a, st);
 }
 
 int mh3d_variants(int) { return 2; }

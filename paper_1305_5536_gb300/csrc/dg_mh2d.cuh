@@ -80,13 +80,15 @@ __device__ __forceinline__ MhMem2D<TC> mh2d_mem(unsigned char* base) {
 // coefficients s[] at centroid primitives W; with limiter 1 the min/max limiter
 // (Sec. 2.5) scales them and s[] receives the limited conserved coefficients
 // (the same arithmetic as limit_cell2d), with limiter 2 the WENO-type limiter
-// does (dg_weno.cuh).  Wn: the 4 face neighbours' primitives.
-template <int EQ, class TC>
+// does (dg_weno.cuh).  Wn: the 4 face neighbours' primitives.  WENO selects the
+// WENO-type limiter at compile time: as a run-time branch its code, even called
+// out of line, raises the register allocation of the min/max kernels by a fifth.
+template <int EQ, class TC, bool WENO>
 __device__ __forceinline__ void mh_grads2d(const Gas<TC>& G, const TC* hh, const TC* W,
                                            const TC (*Wn)[Tr2<EQ>::NP], int limiter, TC* s,
                                            TC* g) {
   constexpr int NP = Tr2<EQ>::NP;
-  if (limiter == 2) {
+  if constexpr (WENO) {
     weno_cell2d<EQ, TC>(G, hh, W, Wn, s, g);
     return;
   }
@@ -239,7 +241,7 @@ __device__ __forceinline__ void face_flux_prim2d(const Gas<TC>& G, int dir, cons
   else { F[1] = Ff[2]; F[2] = Ff[1]; }
 }
 
-template <int EQ, class TC, class TS, int TX, int TY, int NGF>
+template <int EQ, class TC, class TS, int TX, int TY, int NGF, bool WENO>
 __device__ __forceinline__ void mh2d_compute(const Stage2DArgs<TS>& A, int i0, int j0,
                                              unsigned nblk, const MhMem2D<TC>& MM,
                                              TileScalars<TX * TY>& S) {
@@ -301,7 +303,7 @@ __device__ __forceinline__ void mh2d_compute(const Stage2DArgs<TS>& A, int i0, i
     }
 #pragma unroll
     for (int k = 0; k < NS; ++k) s[k] = s_sl[k * R1 + r1];
-    mh_grads2d<EQ, TC>(G, hh, W, Wn, A.limiter, s, g);
+    mh_grads2d<EQ, TC, WENO>(G, hh, W, Wn, A.limiter, s, g);
     mh_rates2d<EQ, TC>(G, W, g, Wt);
 #pragma unroll
     for (int k = 0; k < NS; ++k) { s_sl[k * R1 + r1] = s[k]; s_g[k * R1 + r1] = g[k]; }
@@ -417,7 +419,7 @@ __device__ __forceinline__ void mh2d_compute(const Stage2DArgs<TS>& A, int i0, i
   courant_commit2d<EQ, TC, TS, NT>(A, G, owner, o0, dx, dy, dt, nblk, err, S);
 }
 
-template <int EQ, class TC, class TS, int TX, int TY, int NGF>
+template <int EQ, class TC, class TS, int TX, int TY, int NGF, bool WENO>
 __global__ void __launch_bounds__(TX * TY) mh2d_kernel(const Stage2DArgs<TS> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ TileScalars<TX * TY> S;
@@ -427,7 +429,7 @@ __global__ void __launch_bounds__(TX * TY) mh2d_kernel(const Stage2DArgs<TS> A) 
   __syncthreads();
   stage2d_load<EQ, TC, TS, TX, TY>(A, M.m);
   __syncthreads();
-  mh2d_compute<EQ, TC, TS, TX, TY, NGF>(A, i0, j0, gridDim.x * gridDim.y, M, S);
+  mh2d_compute<EQ, TC, TS, TX, TY, NGF, WENO>(A, i0, j0, gridDim.x * gridDim.y, M, S);
 }
 
 }  // namespace dgk

@@ -40,11 +40,12 @@ __host__ __device__ constexpr size_t mh3d_smem_bytes() {
 // Primitive gradients g[v*3+d] (v = rho, vx, vy, vz, p) of one cell from its
 // conserved coefficients s[] at centroid primitives W; limiter 1: the min/max
 // limiter scales them, 2: the WENO-type limiter (dg_weno.cuh) replaces them (Wn:
-// the 6 face neighbours' primitives).
-template <class TC>
+// the 6 face neighbours' primitives).  WENO selects the WENO-type limiter at
+// compile time, so that the min/max kernels keep their register allocation.
+template <class TC, bool WENO>
 __device__ __forceinline__ void mh_grads3d(const Gas<TC>& G, const TC* hh, const TC* W,
                                            const TC (*Wn)[5], int limiter, const TC* s, TC* g) {
-  if (limiter == 2) {
+  if constexpr (WENO) {
     TC sc[15];
 #pragma unroll
     for (int k = 0; k < 15; ++k) sc[k] = s[k];
@@ -175,7 +176,7 @@ __device__ __forceinline__ void gather3d_centroid(const TC* s_f, int FMAX, int f
   }
 }
 
-template <class TC, class TS, int TX, int TY, int TZ, int NGF>
+template <class TC, class TS, int TX, int TY, int TZ, int NGF, bool WENO>
 __global__ void __launch_bounds__(TX * TY * TZ) mh3d_kernel(const Stage3DArgs<TS> A) {
   constexpr int R2X = TX + 4, R2Y = TY + 4, R2Z = TZ + 4, R2 = R2X * R2Y * R2Z;
   constexpr int R1X = TX + 2, R1Y = TY + 2, R1Z = TZ + 2, R1 = R1X * R1Y * R1Z;
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) mh3d_kernel(const Stage3DArgs<TS
     }
 #pragma unroll
     for (int k = 0; k < 15; ++k) s[k] = s_g[k * R1 + r1];
-    mh_grads3d<TC>(G, hh, W, Wn, A.limiter, s, g);
+    mh_grads3d<TC, WENO>(G, hh, W, Wn, A.limiter, s, g);
     mh_rates3d<TC>(G, W, g, Wt);
 #pragma unroll
     for (int k = 0; k < 15; ++k) s_g[k * R1 + r1] = g[k];
