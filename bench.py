@@ -103,7 +103,7 @@ def _src_sha(kernel):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1305_5536_gb300", "csrc")
     fam = _FAMILY_SOURCES.get(kernel.split()[0], ())
-    for f in sorted(fam + ("dg_physics.cuh", "dg_common.cuh")):
+    for f in sorted(fam + ("dg_physics.cuh", "dg_common.cuh", "dg_weno.cuh")):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
