@@ -68,7 +68,7 @@ enum { DG_EXACT = 0, DG_HLLD = 1 };
 enum { DG_SSPRK2 = 0, DG_MUSCL_HANCOCK = 1 };
 
 typedef struct {
-  int eq;           /* DG_EULER | DG_MHD (MHD: dim 2 only) */
+  int eq;           /* DG_EULER | DG_MHD (3D MHD: limiter 0 or 1) */
   int dim;          /* 2 | 3 */
   int n[3];         /* cells per axis (n[2] ignored in 2D) */
   double box[3];    /* box lengths; cell size box[a]/n[a] */

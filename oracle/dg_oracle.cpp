@@ -101,7 +101,7 @@ enum {
   FLAG_NONPHYS = 1,     // rho <= 0 or p <= 0 where a state is evaluated
   FLAG_VACUUM = 2,      // exact Riemann solver: vacuum generated
   FLAG_NEWTON = 4,      // exact Riemann solver: Newton iteration did not converge
-  FLAG_UNSUPPORTED = 8, // a combination the oracle does not define (WENO, 3D field)
+  FLAG_UNSUPPORTED = 8, // a combination the oracle does not define (none at present)
 };
 
 struct Cfg {
@@ -737,6 +737,8 @@ void primitive_gradients(const R W[8], const R dU[8][3], double g, R dW[8][3]) {
   }
 }
 
+static void invert_small(int m, const double* A, double* Ainv);
+
 template <class R>
 void limit_state(const Grid& G, const R* u, R* out, int& flags) {
   const long n = G.ncell;
@@ -792,7 +794,7 @@ void limit_state(const Grid& G, const R* u, R* out, int& flags) {
     R aB(1.0);
     R aBk[8];  // the limited magnetic derivative coefficients
     const int nBd = G.L.nB - G.L.nBa;
-    if (G.c.limiter == 2 && !(mhd && dim == 3)) {
+    if (G.c.limiter == 2) {
       // Sec. 2.5, the WENO-type limiter.  Per primitive, two candidate gradients:
       // the unlimited DG gradient and the stencil gradient of the FV method (the
       // central difference of the face neighbours' centroid values, min/max
@@ -826,7 +828,66 @@ void limit_state(const Grid& G, const R* u, R* out, int& flags) {
         R ws = 1.0 / r_sqrt(eps + osc(q, gs));
         for (int d = 0; d < dim; ++d) dWl[q][d] = (wd * dW[q][d] + ws * gs[d]) / (wd + ws);
       }
-      if (mhd) {
+      if (mhd && dim == 3) {
+        // 3D: the stencil gradients G[i] of B_i, each min/max limited as in the FV
+        // method, projected in L2 over the cell onto the span of the basis
+        // functions' gradients: the coefficients c minimise
+        //   int |sum_k c_k (grad V_k) x - G x|^2 dOmega
+        //     = (V/12) sum_{i,d} h_d^2 (sum_k c_k dV_k,i/dx_d - G[i][d])^2,
+        // i.e. the normal equations N c = r with N_kl = sum_{i,d} h_d^2 dV_k,i/dx_d
+        // dV_l,i/dx_d and r_k = sum_{i,d} h_d^2 dV_k,i/dx_d G[i][d]
+        R Gs[3][3];
+        for (int i = 0; i < 3; ++i) {
+          stencil(5 + i, Gs[i]);
+          R a = alpha_of(5 + i, Gs[i]);
+          for (int e = 0; e < 3; ++e) Gs[i][e] = a * Gs[i][e];
+        }
+        double N[64], Ninv[64];
+        for (int k = 0; k < nBd; ++k)
+          for (int l = 0; l < nBd; ++l) {
+            double s = 0.0;
+            for (int i = 0; i < 3; ++i)
+              for (int e = 0; e < 3; ++e)
+                s += G.h[e] * G.h[e] * mag_dw(3, G.L.nBa + k, i, e) * mag_dw(3, G.L.nBa + l, i, e);
+            N[k * nBd + l] = s;
+          }
+        invert_small(nBd, N, Ninv);
+        R rr[8], st[8];
+        for (int k = 0; k < nBd; ++k) {
+          rr[k] = R(0.0);
+          for (int i = 0; i < 3; ++i)
+            for (int e = 0; e < 3; ++e)
+              rr[k] = rr[k] + G.h[e] * G.h[e] * mag_dw(3, G.L.nBa + k, i, e) * Gs[i][e];
+        }
+        for (int k = 0; k < nBd; ++k) {
+          st[k] = R(0.0);
+          for (int l = 0; l < nBd; ++l) st[k] = st[k] + Ninv[k * nBd + l] * rr[l];
+        }
+        // the projected stencil field's gradients, for its oscillation factor
+        R sB[3][3];
+        for (int i = 0; i < 3; ++i)
+          for (int e = 0; e < 3; ++e) {
+            sB[i][e] = R(0.0);
+            for (int k = 0; k < nBd; ++k) sB[i][e] = sB[i][e] + st[k] * mag_dw(3, G.L.nBa + k, i, e);
+          }
+        // one weight pair for the field (oscillation factors of its three
+        // components added), so that the blend stays divergence free
+        R od(0.0), os(0.0);
+        for (int i = 0; i < 3; ++i) {
+          od = od + osc(5 + i, dW[5 + i]);
+          os = os + osc(5 + i, sB[i]);
+        }
+        R wd = 1.0 / r_sqrt(eps + od);
+        R ws = 1.0 / r_sqrt(eps + os);
+        for (int k = 0; k < nBd; ++k)
+          aBk[k] = (wd * u[(long)(b0 + G.L.nBa + k) * n + c] + ws * st[k]) / (wd + ws);
+        for (int i = 0; i < 3; ++i)
+          for (int e = 0; e < 3; ++e) {
+            dWl[5 + i][e] = R(0.0);
+            for (int k = 0; k < nBd; ++k)
+              dWl[5 + i][e] = dWl[5 + i][e] + aBk[k] * mag_dw(3, G.L.nBa + k, i, e);
+          }
+      } else if (mhd) {
         // stencil gradients of Bx and By, each min/max limited as in the FV
         // method, then projected in L2 over the cell onto the divergence-free
         // basis: a1 = dBx/dy, a2 = dBy/dx, a3 = (dBx/dx dx^2 - dBy/dy dy^2)/(dx^2 + dy^2)
@@ -857,7 +918,6 @@ void limit_state(const Grid& G, const R* u, R* out, int& flags) {
       }
       if (mhd) {
         // one factor for the whole field: min over its components (2D: Bx, By)
-        if (G.c.limiter == 2) flags |= FLAG_UNSUPPORTED;  // 3D field: min/max instead
         aB = alpha_of(5, dW[5]);
         for (int q = 1; q < G.L.nBa; ++q) aB = r_min(aB, alpha_of(5 + q, dW[5 + q]));
         for (int q = 0; q < G.L.nBa; ++q)

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdg.so")
 SOURCES = ["dg_capi.cu", "dg_misc.cu", "dg_k2d.cu", "dg_k3d.cu", "dg_k3m.cu", "dg_kmh.cu", "dg_kmh3d.cu",
-           "dg_adjoint.cu",
+           "dg_kmh3m.cu", "dg_adjoint.cu",
            "dg_noalloc.cu", "dg_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -39,7 +39,8 @@ def _deps_mtime():
 # Forward stage kernels: FP32 division and square root to within 2 ulp (the
 # single-precision path only; double precision is always IEEE-exact).
 FAST_FP32 = ["-prec-div=false", "-prec-sqrt=false"]
-FAST_FP32_SOURCES = ("dg_k2d.cu", "dg_k3d.cu", "dg_k3m.cu", "dg_kmh.cu", "dg_kmh3d.cu", "dg_batch.cu")
+FAST_FP32_SOURCES = ("dg_k2d.cu", "dg_k3d.cu", "dg_k3m.cu", "dg_kmh.cu", "dg_kmh3d.cu", "dg_kmh3m.cu",
+                     "dg_batch.cu")
 
 
 def _compile(src, extra):

@@ -128,10 +128,6 @@ const char* validate(const dg_config* c) {
   if (c->ckpt_every < 0) return "ckpt_every must be >= 0";
   if (c->integrator != DG_SSPRK2 && c->integrator != DG_MUSCL_HANCOCK)
     return "integrator must be DG_SSPRK2 or DG_MUSCL_HANCOCK";
-  if (c->eq == DG_MHD && c->dim == 3 && c->integrator != DG_SSPRK2)
-    return "3D MHD is stepped with the SSP-RK2 integrator";
-  if (c->eq == DG_MHD && c->dim == 3 && c->limiter == 2)
-    return "3D MHD takes limiter 0 or 1 (the WENO-type limiter covers 2D MHD and Euler)";
   if (c->face_points < 0 || c->face_points > 2) return "face_points must be 0, 1 or 2";
   if (c->integrator == DG_SSPRK2 && c->face_points == 1)
     return "the SSP-RK2 step uses the Gauss face rule (face_points 0 or 2)";
@@ -298,7 +294,8 @@ cudaError_t launch_mh_t(dg_ctx* c, int a, int b, double dtov) {
       s.out = sbuf<TS>(c, b, p);
       s.lim_sl = nullptr;
       s.ctl = c->ctl + ip;
-      cudaError_t e = launch_mh3d(v, c->face_points, s, c->launch_stream);
+      cudaError_t e = c->eq == DG_MHD ? launch_mh3m(v, c->face_points, s, c->launch_stream)
+                                      : launch_mh3d(v, c->face_points, s, c->launch_stream);
       if (e != cudaSuccess) return e;
       continue;
     }
@@ -480,7 +477,8 @@ void tune_save() {
 dg_status autotune(dg_ctx* c) {
   if (c->variant >= 0) return DG_OK;
   int nvar = c->integrator == DG_MUSCL_HANCOCK
-                 ? (c->dim == 2 ? mh2d_variants(c->eq, c->fp32) : mh3d_variants(c->fp32))
+                 ? (c->dim == 2 ? mh2d_variants(c->eq, c->fp32)
+                    : (c->eq == DG_MHD ? mh3m_variants(c->fp32) : mh3d_variants(c->fp32)))
              : c->batch2d ? kBatchVariants
              : (c->dim == 2 ? stage2d_variants(c->eq, c->fp32)
                 : (c->eq == DG_MHD ? stage3m_variants(c->fp32) : stage3d_variants(c->fp32)));
@@ -871,6 +869,9 @@ const char* dg_kernel_name(const dg_ctx* cc) {
   char b[96];
   if (c->integrator == DG_MUSCL_HANCOCK && c->dim == 2)
     snprintf(b, sizeof(b), "mh2d_kernel %s %s %dpt", mh2d_variant_name(c->eq, c->fp32, v), prec,
+             c->face_points);
+  else if (c->integrator == DG_MUSCL_HANCOCK && c->eq == DG_MHD)
+    snprintf(b, sizeof(b), "mh3m_kernel %s %s %dpt", mh3m_variant_name(c->fp32, v), prec,
              c->face_points);
   else if (c->integrator == DG_MUSCL_HANCOCK)
     snprintf(b, sizeof(b), "mh3d_kernel %s %s %dpt", mh3d_variant_name(c->fp32, v), prec,

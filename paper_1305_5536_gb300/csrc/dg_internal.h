@@ -48,6 +48,12 @@ cudaError_t launch_mh3d(int variant, int face_points, const Stage3DArgs<double>&
                         cudaStream_t st);
 cudaError_t launch_mh3d(int variant, int face_points, const Stage3DArgs<float>& a,
                         cudaStream_t st);
+int mh3m_variants(int fp32);
+const char* mh3m_variant_name(int fp32, int v);
+cudaError_t launch_mh3m(int variant, int face_points, const Stage3DArgs<double>& a,
+                        cudaStream_t st);
+cudaError_t launch_mh3m(int variant, int face_points, const Stage3DArgs<float>& a,
+                        cudaStream_t st);
 
 // Layout conversion of one interchange plane (ncell doubles) to/from the state.
 template <class TS>

@@ -162,14 +162,14 @@ __device__ __forceinline__ void face_flux_prim3d(const Gas<TC>& G, int d, const 
 }
 
 // Add the two face-centroid fluxes of orientation D of a cell to its right-hand
-// side (gather3d with four equal Gauss-point fluxes).
-template <int D, class TC>
+// side (gather3d with four equal Gauss-point fluxes) for NV variables.
+template <int D, class TC, int NV = 5>
 __device__ __forceinline__ void gather3d_centroid(const TC* s_f, int FMAX, int fm, int fp,
                                                   const TC* hd, TC* rc0, TC* rs) {
   const TC c0f = TC(1) / hd[D];
   const TC csf = TC(6) / (hd[D] * hd[D]);
 #pragma unroll
-  for (int v = 0; v < 5; ++v) {
+  for (int v = 0; v < NV; ++v) {
     const TC m = s_f[v * FMAX + fm], p = s_f[v * FMAX + fp];
     rc0[v] -= (p - m) * c0f;
     rs[3 * v + D] -= csf * (p + m);

@@ -129,6 +129,115 @@ __device__ __forceinline__ void limit_cell3m(const Gas<TC>& G, const TC* hh, con
   for (int k = 15; k < 23; ++k) s[k] *= aB;
 }
 
+// WENO-type limiter of one cell (Sec. 2.5, dg_weno.cuh): the primitives rho, v, p
+// blend their DG gradient with their min/max-limited central difference by the
+// oscillation weights.  The field has one weight pair: its stencil candidate is
+// the min/max-limited central differences G[i][d] of B_i, projected in L2 over
+// the cell onto the divergence-free basis; the cross derivatives are basis
+// coefficients themselves (a4 = G_xy, a5 = G_xz, a6 = G_yx, a7 = G_yz,
+// a8 = G_zx, a9 = G_zy) and (a10, a11) solve
+//   [[hx^2 + hy^2, hx^2], [hx^2, hx^2 + hz^2]] (a10, a11)
+//     = (hx^2 G_xx - hy^2 G_yy, hx^2 G_xx - hz^2 G_zz),
+// and the oscillation factors of the three components are added.  s[23] is
+// limited in place (product rule back as in limit_cell3m).
+template <class TC>
+__device__ __forceinline__ void weno_cell3m(const Gas<TC>& G, const TC* hh, const TC* W,
+                                            const TC (*Wn)[8], TC* s) {
+  TC hi[8], lo[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    TC a = W[q], b = W[q];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      a = Wn[k][q] > a ? Wn[k][q] : a;
+      b = Wn[k][q] < b ? Wn[k][q] : b;
+    }
+    hi[q] = a;
+    lo[q] = b;
+  }
+  const TC rho = W[0], inv = TC(1) / rho;
+  const TC v[3] = {W[1], W[2], W[3]};
+  const TC v2h = TC(0.5) * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  TC gB[3][3];
+  field_grad3m<TC>(s, gB);
+  TC g[5][3];  // primitive gradients of rho, vx, vy, vz, p
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    g[0][d] = s[d];
+    TC vdv = TC(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      g[1 + i][d] = (s[3 * (1 + i) + d] - v[i] * g[0][d]) * inv;
+      vdv += v[i] * g[1 + i][d];
+    }
+    const TC BdB = W[5] * gB[0][d] + W[6] * gB[1][d] + W[7] * gB[2][d];
+    g[4][d] = G.gm1 * (s[12 + d] - v2h * g[0][d] - rho * vdv - BdB);
+  }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    TC nb[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) nb[k] = Wn[k][q];
+    weno_blend<TC, 3>(W[q], hi[q], lo[q], nb, hh, g[q]);
+  }
+  // the field: stencil candidate, its projection, one weight pair
+  TC Gs[3][3], od = TC(0), os = TC(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    TC nb[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) nb[k] = Wn[k][5 + i];
+    weno_stencil<TC, 3>(W[5 + i], hi[5 + i], lo[5 + i], nb, hh, Gs[i]);
+    od += weno_osc<TC, 3>(W[5 + i], nb, gB[i], hh);
+  }
+  const TC hx2 = hh[0] * hh[0], hy2 = hh[1] * hh[1], hz2 = hh[2] * hh[2];
+  const TC P = hx2 * Gs[0][0] - hy2 * Gs[1][1], Q = hx2 * Gs[0][0] - hz2 * Gs[2][2];
+  const TC Am = hx2 + hy2, Bm = hx2 + hz2;
+  const TC idet = TC(1) / (Am * Bm - hx2 * hx2);
+  TC st[23];  // the projected stencil field in slots 15..22
+  st[15] = Gs[0][1]; st[16] = Gs[0][2]; st[17] = Gs[1][0];
+  st[18] = Gs[1][2]; st[19] = Gs[2][0]; st[20] = Gs[2][1];
+  st[21] = (Bm * P - hx2 * Q) * idet;
+  st[22] = (Am * Q - hx2 * P) * idet;
+  TC sB[3][3];
+  field_grad3m<TC>(st, sB);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    TC nb[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) nb[k] = Wn[k][5 + i];
+    os += weno_osc<TC, 3>(W[5 + i], nb, sB[i], hh);
+  }
+  const TC wd = TC(1) / sqrt(TC(kWenoEps) + od);
+  const TC ws = TC(1) / sqrt(TC(kWenoEps) + os);
+  const TC iw = TC(1) / (wd + ws);
+#pragma unroll
+  for (int k = 15; k < 23; ++k) s[k] = (wd * s[k] + ws * st[k]) * iw;
+  field_grad3m<TC>(s, gB);  // the limited field's gradients
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const TC r = g[0][d];
+    TC vdv = TC(0);
+    s[d] = r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const TC u = g[1 + i][d];
+      s[3 * (1 + i) + d] = rho * u + v[i] * r;
+      vdv += v[i] * u;
+    }
+    const TC BdB = W[5] * gB[0][d] + W[6] * gB[1][d] + W[7] * gB[2][d];
+    s[12 + d] = g[4][d] * G.inv_gm1 + v2h * r + rho * vdv + BdB;
+  }
+}
+
+// The limiter of the kernels: WENO (compile time) selects the WENO-type one.
+template <class TC, bool WENO>
+__device__ __forceinline__ void limit3m(const Gas<TC>& G, const TC* hh, const TC* W,
+                                        const TC (*Wn)[8], TC* s) {
+  if constexpr (WENO) weno_cell3m<TC>(G, hh, W, Wn, s);
+  else limit_cell3m<TC>(G, hh, W, Wn, s);
+}
+
 // Conserved values (rho, mx, my, mz, E, Bx, By, Bz) of the cell polynomial at
 // local point (x, y, z).
 template <class TC>
@@ -164,17 +273,13 @@ __device__ __forceinline__ void phys_flux3m(const Gas<TC>& G, const TC* c, int d
   F[4] = (c[4] + pT) * vd - Bd * vB;
 }
 
-// HLLD flux through a face along axis d (uniform across the CTA) between
-// conserved cl, cr, with the normal field replaced by the average of both sides
-// (Sec. 2.6); lab frame, component order of phys_flux3m.  The face frame is
-// (n, t1, t2) = (d, d+1, d+2) cyclically, picked with selects.
+// HLLD flux through a face along axis d (uniform across the CTA) between the
+// primitive states Wl, Wr (rho, v, p, B), with the normal field replaced by the
+// average of both sides (Sec. 2.6); lab frame, component order of phys_flux3m.
+// The face frame is (n, t1, t2) = (d, d+1, d+2) cyclically, picked with selects.
 template <class TC>
-__device__ __forceinline__ void face_flux3m(const Gas<TC>& G, int d, const TC* cl, const TC* cr,
-                                            TC* F, unsigned& err) {
-  TC Wl[8], Wr[8];
-  unsigned e2 = 0;
-  prims3m<TC>(G, cl, Wl, e2);
-  prims3m<TC>(G, cr, Wr, e2);
+__device__ __forceinline__ void face_flux_prim3m(const Gas<TC>& G, int d, const TC* Wl,
+                                                 const TC* Wr, TC* F, unsigned& err) {
   auto pick = [&](const TC* W, int o, int k) {  // component k (0 n, 1 t1, 2 t2) of W[o..o+2]
     const int a = d + k >= 3 ? d + k - 3 : d + k;
     return a == 0 ? W[o] : (a == 1 ? W[o + 1] : W[o + 2]);
@@ -195,6 +300,17 @@ __device__ __forceinline__ void face_flux3m(const Gas<TC>& G, int d, const TC* c
   }
 }
 
+// The same between conserved states cl, cr (the solver checks positivity).
+template <class TC>
+__device__ __forceinline__ void face_flux3m(const Gas<TC>& G, int d, const TC* cl, const TC* cr,
+                                            TC* F, unsigned& err) {
+  TC Wl[8], Wr[8];
+  unsigned e2 = 0;
+  prims3m<TC>(G, cl, Wl, e2);
+  prims3m<TC>(G, cr, Wr, e2);
+  face_flux_prim3m<TC>(G, d, Wl, Wr, F, err);
+}
+
 // Field part of the right-hand side from the Taylor-like gathers r[3*(5+i)+d].
 template <class TC>
 __device__ __forceinline__ void field_rhs3m(const TC* rs24, const TC* hd, TC* ra) {
@@ -210,7 +326,7 @@ __device__ __forceinline__ void field_rhs3m(const TC* rs24, const TC* hd, TC* ra
   ra[7] = (A * Q - hx2 * P) / det;
 }
 
-template <class TC, class TS, int TX, int TY, int TZ, int STAGE>
+template <class TC, class TS, int TX, int TY, int TZ, int STAGE, bool WENO>
 __global__ void __launch_bounds__(TX * TY * TZ) stage3m_kernel(const Stage3DArgs<TS> A) {
   constexpr int R2X = TX + 4, R2Y = TY + 4, R2Z = TZ + 4, R2 = R2X * R2Y * R2Z;
   constexpr int R1X = TX + 2, R1Y = TY + 2, R1Z = TZ + 2, R1 = R1X * R1Y * R1Z;
@@ -300,7 +416,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3m_kernel(const Stage3DArgs
       }
 #pragma unroll
       for (int k = 0; k < 23; ++k) s[k] = s_sl[k * R1 + r1];
-      limit_cell3m<TC>(G, hh, W, Wn, s);
+      limit3m<TC, WENO>(G, hh, W, Wn, s);
 #pragma unroll
       for (int k = 0; k < 23; ++k) s_sl[k * R1 + r1] = s[k];
     }
@@ -432,7 +548,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3m_kernel(const Stage3DArgs
         for (int v = 0; v < 8; ++v) c[v] = Cvt<TC>::to_tc(A.base.c0[v * ncell + nb[k]]);
         prims3m<TC>(G, c, Wn[k], err);
       }
-      limit_cell3m<TC>(G, hh, W, Wn, sn);
+      limit3m<TC, WENO>(G, hh, W, Wn, sn);
     }
 #pragma unroll
     for (int v = 0; v < 8; ++v)

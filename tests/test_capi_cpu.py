@@ -31,12 +31,14 @@ def test_num_planes_and_validation():
     for eq, dim, n in ((0, 2, 12), (0, 3, 20), (1, 2, 17), (1, 3, 31)):
         c = dg.make_config("mhd" if eq else "euler", dim, (8, 8, 8))
         assert lib.dg_num_planes(ctypes.byref(c)) == n
-    # combinations that are not built: 3D MHD with the MUSCL-Hancock step or the
-    # WENO-type limiter; the SSP-RK2 step with the face-centroid rule
-    bad = dg.make_config("mhd", 3, (8, 8, 8), integrator="mh")
-    assert lib.dg_num_planes(ctypes.byref(bad)) == -1
-    bad = dg.make_config("mhd", 3, (8, 8, 8), limiter=2)
-    assert lib.dg_num_planes(ctypes.byref(bad)) == -1
+    # every equation set takes both integrators and every limiter
+    for lim in (0, 1, 2):
+        c = dg.make_config("mhd", 3, (8, 8, 8), limiter=lim)
+        assert lib.dg_num_planes(ctypes.byref(c)) == 31
+        for fp in (0, 1, 2):
+            c = dg.make_config("mhd", 3, (8, 8, 8), limiter=lim, integrator="mh", face_points=fp)
+            assert lib.dg_num_planes(ctypes.byref(c)) == 31
+    # not built: the SSP-RK2 step with the face-centroid rule
     bad = dg.make_config("euler", 2, (8, 8), face_points=1)
     assert lib.dg_num_planes(ctypes.byref(bad)) == -1
     bad = dg.make_config("euler", 2, (8, 8))
