@@ -10,25 +10,31 @@
  *   Sec. 2.2  weak form (eq. `dg`); per cell a Taylor polynomial about the
  *             centroid, U = U_avg + dU/dx x + dU/dy y [+ dU/dz z]; evolution of
  *             averages (eq. `fv`, `fv3d`) and derivatives (eq. `dgderiv`,
- *             `dgderiv3d`) with the cell mass matrix; in 2D MHD the magnetic field
- *             uses the locally divergence-free basis V1..V5:
- *             Bx = b1 + a3 x + a1 y,  By = b2 + a2 x - a3 y.
- *   Sec. 2.3  face fluxes from the exact Riemann solver (Euler) or HLLD (MHD),
- *             here at 2 Gauss points per face dimension.
- *   Sec. 2.5  min/max slope limiter on primitive variables, applied to every
- *             stage input.
+ *             `dgderiv3d`) with the cell mass matrix; the magnetic field uses the
+ *             locally divergence-free bases, V1..V5 in 2D:
+ *             Bx = b1 + a3 x + a1 y,  By = b2 + a2 x - a3 y,
+ *             and V1..V11 in 3D:
+ *             Bx = b1 + (a10 + a11) x + a4 y + a5 z,  By = b2 + a6 x - a10 y + a7 z,
+ *             Bz = b3 + a8 x + a9 y - a11 z.
+ *   Sec. 2.3  face fluxes from the exact Riemann solver (Euler) or HLLD (MHD).
+ *   Sec. 2.4  time integration: the two-stage SSP Runge-Kutta method (Gauss face
+ *             rules), or the paper's MUSCL-Hancock step (half-step primitive
+ *             prediction, one update; face-centroid or Gauss face rule).
+ *   Sec. 2.5  slope limiting on primitive variables at every stage input: the
+ *             min/max limiter or the WENO-type limiter.
  *   Sec. 2.6  the normal field at a face is the average of both sides.
- *   Time integration: two-stage SSP Runge-Kutta (the traditional DG integrator
- *   named in Sec. 2.4); time step dt = CFL / max_cells sum_d (|v_d| + c_d)/dx_d.
+ *   Time step dt = CFL / max_cells sum_d (|v_d| + c_d)/dx_d (c: sound speed, or
+ *   the fast magnetosonic speed along d).
  *
  * Interchange layout (every state buffer crossing this ABI): float64, one plane
  * per coefficient, planes variable-major, each plane [nz][ny][nx] with x fastest.
  *   Taylor variables, in order: 2D Euler (rho, mx, my, E), 3D Euler
- *   (rho, mx, my, mz, E), 2D MHD (rho, mx, my, E); per variable the coefficients
- *   (average, d/dx, d/dy[, d/dz]) in physical units -> plane v*(dim+1)+k.
- *   2D MHD then appends the magnetic block (b1, b2, a1, a2, a3).
- *   Number of planes: 12 (2D Euler), 20 (3D Euler), 17 (2D MHD); see
- *   dg_num_planes().
+ *   (rho, mx, my, mz, E), 2D MHD (rho, mx, my, E), 3D MHD (rho, mx, my, mz, E);
+ *   per variable the coefficients (average, d/dx, d/dy[, d/dz]) in physical
+ *   units -> plane v*(dim+1)+k.  MHD then appends the magnetic block:
+ *   (b1, b2, a1, a2, a3) in 2D, (b1, b2, b3, a4, ..., a11) in 3D.
+ *   Number of planes: 12 (2D Euler), 20 (3D Euler), 17 (2D MHD), 31 (3D MHD);
+ *   see dg_num_planes().
  *
  * Ownership: the caller owns every buffer it passes; the library copies in and
  * out and owns its device state.  Streams: all device work is enqueued on the
