@@ -262,22 +262,64 @@ __device__ __forceinline__ void stage2d_setup(const Stage2DArgs<TS>& A, int i0, 
   else if (tid < T::R2X + T::R2Y) M.gy[tid - T::R2X] = wrap_index(j0 - 2 + (tid - T::R2X), A.ny) * A.nx;
 }
 
+// Global -> shared copy of one 4- or 8-byte element without a register round
+// trip (cp.async); cp_async_wait_all() waits for this thread's copies.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
+  static_assert(BYTES == 4 || BYTES == 8, "element copies of 4 or 8 bytes");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // Stage the tile from global memory element by element (periodic wrap): averages
-// with halo 2, derivative coefficients with halo 1.  The caller synchronises.
+// with halo 2, derivative coefficients with halo 1.  Every load of a thread is
+// in flight before the first one is used, so that their DRAM latencies overlap:
+// plain copies go through cp.async, and the FP64 averages of the FP32 path are
+// loaded into registers in chunks of 8 and converted after each chunk.  The
+// caller synchronises.
 template <int EQ, class TC, class TS, int TX, int TY>
 __device__ __forceinline__ void stage2d_load(const Stage2DArgs<TS>& A, const TileMem<TC>& M) {
   using T = Tile2D<EQ, TX, TY>;
+  static_assert(sizeof(TS) == sizeof(TC), "derivative coefficients are staged as stored");
+  constexpr int N0 = T::NV * T::R2, N1 = T::NS * T::R1;
   const size_t ncell = (size_t)A.ncell;
-  for (int e = threadIdx.x; e < T::NV * T::R2; e += T::NT) {
-    int v = e / T::R2, r = e - v * T::R2;
-    int ry = r / T::R2X, rx = r - ry * T::R2X;
-    M.c0[e] = Cvt<TC>::to_tc(__ldg(&A.in.c0[v * ncell + M.gy[ry] + M.gx[rx]]));
-  }
-  for (int e = threadIdx.x; e < T::NS * T::R1; e += T::NT) {
+  for (int e = threadIdx.x; e < N1; e += T::NT) {
     int v = e / T::R1, r = e - v * T::R1;
     int ry = r / T::R1X, rx = r - ry * T::R1X;
-    M.sl[e] = (TC)__ldg(&A.in.sl[v * ncell + M.gy[ry + 1] + M.gx[rx + 1]]);
+    cp_async_elem<sizeof(TS)>(&M.sl[e], &A.in.sl[v * ncell + M.gy[ry + 1] + M.gx[rx + 1]]);
   }
+  if constexpr (sizeof(TC) == 8) {
+    for (int e = threadIdx.x; e < N0; e += T::NT) {
+      int v = e / T::R2, r = e - v * T::R2;
+      int ry = r / T::R2X, rx = r - ry * T::R2X;
+      cp_async_elem<8>(&M.c0[e], &A.in.c0[v * ncell + M.gy[ry] + M.gx[rx]]);
+    }
+  } else {
+    constexpr int I0 = (N0 + T::NT - 1) / T::NT, CH = 8;  // loads in flight per chunk
+#pragma unroll
+    for (int i0 = 0; i0 < I0; i0 += CH) {
+      double a[CH];
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        const int e = threadIdx.x + (i0 + i) * T::NT;
+        if (i0 + i < I0 && e < N0) {
+          int v = e / T::R2, r = e - v * T::R2;
+          int ry = r / T::R2X, rx = r - ry * T::R2X;
+          a[i] = __ldg(&A.in.c0[v * ncell + M.gy[ry] + M.gx[rx]]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        const int e = threadIdx.x + (i0 + i) * T::NT;
+        if (i0 + i < I0 && e < N0) M.c0[e] = Cvt<TC>::to_tc(a[i]);
+      }
+    }
+  }
+  cp_async_wait_all();
 }
 
 // End of a step on one tile: the Courant signal speed of the new averages o0[]
