@@ -87,4 +87,23 @@ __host__ __device__ __forceinline__ int wrap_index(int g, int n) {
   return r < 0 ? r + n : r;
 }
 
+// Global -> shared copy of one 4- or 8-byte element without a register round
+// trip (cp.async); cp_async_wait_all() waits for this thread's copies.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
+  static_assert(BYTES == 4 || BYTES == 8, "element copies of 4 or 8 bytes");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Request the line holding `p` into L2 (no register, no wait): for global reads
+// that come later in a kernel, so that they find the line in L2.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+}
+
 }  // namespace dgk

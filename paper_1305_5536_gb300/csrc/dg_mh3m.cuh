@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) mh3m_kernel(const Stage3DArgs<TS
   const TC hdt = TC(0.5) * dtc;
 
   // ---- 1. primitives of the halo-2 box; coefficients of the halo-1 box
+  stage3d_issue<8, 23, TX, TY, TZ>(A.in, ncell, s_gx, s_gy, s_gz, s_g);
   for (int r = tid; r < R2; r += NT) {
     int rz = r / (R2X * R2Y), rr = r - rz * (R2X * R2Y);
     int ry = rr / R2X, rx = rr - ry * R2X;
@@ -210,12 +211,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) mh3m_kernel(const Stage3DArgs<TS
 #pragma unroll
     for (int q = 0; q < 8; ++q) s_w[q * R2 + r] = W[q];
   }
-  for (int e = tid; e < 23 * R1; e += NT) {
-    int v = e / R1, r = e - v * R1;
-    int rz = r / (R1X * R1Y), rr = r - rz * (R1X * R1Y);
-    int ry = rr / R1X, rx = rr - ry * R1X;
-    s_g[e] = (TC)__ldg(&A.in.sl[v * ncell + (size_t)s_gz[rz + 1] + s_gy[ry + 1] + s_gx[rx + 1]]);
-  }
+  cp_async_wait_all();
   __syncthreads();
 
   const TC dx = Cvt<TC>::to_tc(A.dx), dy = Cvt<TC>::to_tc(A.dy), dz = Cvt<TC>::to_tc(A.dz);

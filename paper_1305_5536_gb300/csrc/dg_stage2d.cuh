@@ -262,19 +262,6 @@ __device__ __forceinline__ void stage2d_setup(const Stage2DArgs<TS>& A, int i0, 
   else if (tid < T::R2X + T::R2Y) M.gy[tid - T::R2X] = wrap_index(j0 - 2 + (tid - T::R2X), A.ny) * A.nx;
 }
 
-// Global -> shared copy of one 4- or 8-byte element without a register round
-// trip (cp.async); cp_async_wait_all() waits for this thread's copies.
-template <int BYTES>
-__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
-  static_assert(BYTES == 4 || BYTES == 8, "element copies of 4 or 8 bytes");
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
-
 // Stage the tile from global memory element by element (periodic wrap): averages
 // with halo 2, derivative coefficients with halo 1.  Every load of a thread is
 // in flight before the first one is used, so that their DRAM latencies overlap:
@@ -320,6 +307,22 @@ __device__ __forceinline__ void stage2d_load(const Stage2DArgs<TS>& A, const Til
     }
   }
   cp_async_wait_all();
+}
+
+// Stage 2 reads the step's input state U^n of its own cell only at the end (the
+// Runge-Kutta combination): request those lines into L2 while the tile stages.
+template <int EQ, class TC, class TS, int TX, int TY>
+__device__ __forceinline__ void stage2d_prefetch_base(const Stage2DArgs<TS>& A,
+                                                      const TileMem<TC>& M) {
+  using T = Tile2D<EQ, TX, TY>;
+  const size_t ncell = (size_t)A.ncell;
+  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+  const size_t gc = (size_t)M.gy[ly + 2] + M.gx[lx + 2];
+  const TS* sl = A.limiter && A.lim_sl ? A.lim_sl : A.base.sl;
+#pragma unroll
+  for (int v = 0; v < T::NV; ++v) prefetch_l2(&A.base.c0[v * ncell + gc]);
+#pragma unroll
+  for (int k = 0; k < T::NS; ++k) prefetch_l2(&sl[k * ncell + gc]);
 }
 
 // End of a step on one tile: the Courant signal speed of the new averages o0[]
@@ -625,6 +628,7 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
   const TileMem<TC> M = tile_mem<EQ, TX, TY, TC>(smem_raw);
   stage2d_setup<EQ, TC, TS, TX, TY>(A, i0, j0, M, S);
   __syncthreads();
+  if (STAGE == 2) stage2d_prefetch_base<EQ, TC, TS, TX, TY>(A, M);
   stage2d_load<EQ, TC, TS, TX, TY>(A, M);
   __syncthreads();
   stage2d_compute<EQ, TC, TS, TX, TY, STAGE>(A, i0, j0, nblk, M, S);

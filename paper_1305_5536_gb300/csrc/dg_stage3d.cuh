@@ -183,6 +183,50 @@ __device__ __forceinline__ void gather3d(const TC* s_f, int FMAX, int fm, int fp
   }
 }
 
+// Start of the staging of a 3D tile: the NS derivative coefficients of the
+// halo-1 box are copied with cp.async (in flight while the averages are read),
+// and every average of the halo-2 box that this thread reads next is requested
+// into L2, so that the DRAM latencies of the staging overlap.  The caller then
+// reads the averages, calls cp_async_wait_all() and synchronises.
+template <int NV, int NS, int TX, int TY, int TZ, class TS, class TC>
+__device__ __forceinline__ void stage3d_issue(const StateBuf<TS>& in, size_t ncell,
+                                              const int* s_gx, const int* s_gy, const int* s_gz,
+                                              TC* s_sl) {
+  constexpr int R2X = TX + 4, R2Y = TY + 4, R2 = R2X * R2Y * (TZ + 4);
+  constexpr int R1X = TX + 2, R1Y = TY + 2, R1 = R1X * R1Y * (TZ + 2);
+  constexpr int NT = TX * TY * TZ;
+  static_assert(sizeof(TS) == sizeof(TC), "derivative coefficients are staged as stored");
+  for (int e = threadIdx.x; e < NS * R1; e += NT) {
+    int v = e / R1, r = e - v * R1;
+    int rz = r / (R1X * R1Y), rr = r - rz * (R1X * R1Y);
+    int ry = rr / R1X, rx = rr - ry * R1X;
+    cp_async_elem<sizeof(TS)>(
+        &s_sl[e], &in.sl[v * ncell + (size_t)s_gz[rz + 1] + s_gy[ry + 1] + s_gx[rx + 1]]);
+  }
+  for (int r = threadIdx.x; r < R2; r += NT) {
+    int rz = r / (R2X * R2Y), rr = r - rz * (R2X * R2Y);
+    int ry = rr / R2X, rx = rr - ry * R2X;
+    const size_t g = (size_t)s_gz[rz] + s_gy[ry] + s_gx[rx];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) prefetch_l2(&in.c0[v * ncell + g]);
+  }
+}
+
+// Stage 2 reads the step's input state U^n of its own cell only at the end (the
+// Runge-Kutta combination): request those lines into L2 while the tile stages.
+template <int NV, int NS, int TX, int TY, class TS>
+__device__ __forceinline__ void stage3d_prefetch_base(const Stage3DArgs<TS>& A, size_t ncell,
+                                                      const int* s_gx, const int* s_gy,
+                                                      const int* s_gz) {
+  const int lx = threadIdx.x % TX, ly = (threadIdx.x / TX) % TY, lz = threadIdx.x / (TX * TY);
+  const size_t gc = (size_t)s_gz[lz + 2] + s_gy[ly + 2] + s_gx[lx + 2];
+  const TS* sl = A.limiter && A.lim_sl ? A.lim_sl : A.base.sl;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) prefetch_l2(&A.base.c0[v * ncell + gc]);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) prefetch_l2(&sl[k * ncell + gc]);
+}
+
 // FP32: as many resident CTAs as 80 registers a thread allow (the kernel is
 // latency bound); FP64 keeps its registers.
 template <int NT, class TC>
@@ -231,6 +275,8 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
   __syncthreads();
 
   // ---- primitives of the halo-2 box; averages of the halo-1 box
+  if (STAGE == 2) stage3d_prefetch_base<5, 15, TX, TY>(A, ncell, s_gx, s_gy, s_gz);
+  stage3d_issue<5, 15, TX, TY, TZ>(A.in, ncell, s_gx, s_gy, s_gz, s_sl);
   for (int r = tid; r < R2; r += NT) {
     int rz = r / (R2X * R2Y), rr = r - rz * (R2X * R2Y);
     int ry = rr / R2X, rx = rr - ry * R2X;
@@ -247,12 +293,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
       for (int v = 0; v < 5; ++v) s_c0[v * R1 + r1] = c[v];
     }
   }
-  for (int e = tid; e < 15 * R1; e += NT) {
-    int v = e / R1, r = e - v * R1;
-    int rz = r / (R1X * R1Y), rr = r - rz * (R1X * R1Y);
-    int ry = rr / R1X, rx = rr - ry * R1X;
-    s_sl[e] = (TC)__ldg(&A.in.sl[v * ncell + (size_t)s_gz[rz + 1] + s_gy[ry + 1] + s_gx[rx + 1]]);
-  }
+  cp_async_wait_all();
   __syncthreads();
 
   const TC dx = Cvt<TC>::to_tc(A.dx), dy = Cvt<TC>::to_tc(A.dy), dz = Cvt<TC>::to_tc(A.dz);
