@@ -59,13 +59,15 @@ template <> struct Cvt<double> {
   __device__ __forceinline__ static double to_f64(double x) { return x; }
 };
 template <> struct Cvt<float> {
+  // On the two 32-bit halves: masking the sign of the 64-bit pattern would be
+  // compiled as a double absolute value, an FP64-pipe instruction.
   __device__ __forceinline__ static float to_tc(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long mag = (b & 0x7fffffffffffffffULL) + 0x10000000ULL;
-    const unsigned hi = (unsigned)(mag >> 32), lo = (unsigned)mag;
+    const unsigned h0 = (unsigned)__double2hiint(x), l0 = (unsigned)__double2loint(x);
+    const unsigned lo = l0 + 0x10000000u;                       // round at the float's last bit
+    const unsigned hi = (h0 & 0x7fffffffu) + (lo < l0 ? 1u : 0u);  // magnitude, with the carry
     unsigned r = ((hi - (896u << 20)) << 3) | (lo >> 29);
     r = hi < (897u << 20) ? 0u : r;
-    return __int_as_float((int)(r | ((unsigned)(b >> 32) & 0x80000000u)));
+    return __int_as_float((int)(r | (h0 & 0x80000000u)));
   }
   __device__ __forceinline__ static double to_f64(float f) {
     const unsigned u = (unsigned)__float_as_int(f);
@@ -75,6 +77,18 @@ template <> struct Cvt<float> {
     return m < 0x00800000u ? 0.0 : __hiloint2double((int)hi, (int)lo);
   }
 };
+
+// x / 2 without the FP64 pipe: the exponent field lowered by one (integer work on
+// the high word).  Exact for finite |x| >= 2^-1021; infinities and NaNs are
+// returned as they are; smaller magnitudes (including zero) give a zero of the
+// sign of x.
+__device__ __forceinline__ double half_f64(double x) {
+  const int h = __double2hiint(x), l = __double2loint(x);
+  const int e = h & 0x7ff00000;
+  const bool keep = e == 0x7ff00000, big = e > 0x00100000 && !keep;
+  return __hiloint2double(keep ? h : (big ? h - 0x00100000 : (h & (int)0x80000000)),
+                          keep || big ? l : 0);
+}
 
 // Constants of the equation of state p_gas = (gamma - 1) rho u.
 template <class T>

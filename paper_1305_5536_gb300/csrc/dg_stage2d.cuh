@@ -596,8 +596,8 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v)
-      o0[v] = 0.5 * (A.base.c0[v * ncell + gc] +
-                     fma(dt, Cvt<TC>::to_f64(rc0[v]), A.in.c0[v * ncell + gc]));
+      o0[v] = half_f64(A.base.c0[v * ncell + gc] +
+                       fma(dt, Cvt<TC>::to_f64(rc0[v]), A.in.c0[v * ncell + gc]));
 #pragma unroll
     for (int k = 0; k < NS; ++k) os[k] = TC(0.5) * sn[k] + TC(0.5) * (s[k] + dtc * rs[k]);
   }

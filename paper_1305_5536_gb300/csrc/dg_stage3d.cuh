@@ -459,8 +459,8 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v)
-      o0[v] = 0.5 * (A.base.c0[v * ncell + gc] +
-                     fma(dt, Cvt<TC>::to_f64(rc0[v]), A.in.c0[v * ncell + gc]));
+      o0[v] = half_f64(A.base.c0[v * ncell + gc] +
+                       fma(dt, Cvt<TC>::to_f64(rc0[v]), A.in.c0[v * ncell + gc]));
 #pragma unroll
     for (int k = 0; k < 15; ++k) os[k] = TC(0.5) * sn[k] + TC(0.5) * (s[k] + dtc * rs[k]);
   }

@@ -549,8 +549,8 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3m_kernel(const Stage3DArgs
     }
 #pragma unroll
     for (int v = 0; v < 8; ++v)
-      o0[v] = 0.5 * (A.base.c0[v * ncell + gc] +
-                     fma(dt, Cvt<TC>::to_f64(rc0[v]), A.in.c0[v * ncell + gc]));
+      o0[v] = half_f64(A.base.c0[v * ncell + gc] +
+                       fma(dt, Cvt<TC>::to_f64(rc0[v]), A.in.c0[v * ncell + gc]));
 #pragma unroll
     for (int k = 0; k < 23; ++k)
       os[k] = TC(0.5) * sn[k] + TC(0.5) * (s_sl[k * R1 + r1c] + dtc * rsl[k]);
