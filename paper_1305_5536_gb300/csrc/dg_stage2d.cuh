@@ -262,47 +262,68 @@ __device__ __forceinline__ void stage2d_setup(const Stage2DArgs<TS>& A, int i0, 
   else if (tid < T::R2X + T::R2Y) M.gy[tid - T::R2X] = wrap_index(j0 - 2 + (tid - T::R2X), A.ny) * A.nx;
 }
 
-// Stage the tile from global memory element by element (periodic wrap): averages
-// with halo 2, derivative coefficients with halo 1.  Every load of a thread is
-// in flight before the first one is used, so that their DRAM latencies overlap:
+// Stage the tile from global memory (periodic wrap): averages with halo 2,
+// derivative coefficients with halo 1.  The staged arrays are walked as rows of
+// RX cells: thread t takes column t % RX of every C-th row from row t / RX on
+// (C = NT / RX rows per pass), so its column's global offset is looked up once
+// and a row costs one lookup of the row offset.  Every load of a thread is in
+// flight before the first one is used, so that their DRAM latencies overlap:
 // plain copies go through cp.async, and the FP64 averages of the FP32 path are
-// loaded into registers in chunks of 8 and converted after each chunk.  The
-// caller synchronises.
+// loaded into registers in chunks of 8 passes and converted after each chunk.
+// The caller synchronises.
 template <int EQ, class TC, class TS, int TX, int TY>
 __device__ __forceinline__ void stage2d_load(const Stage2DArgs<TS>& A, const TileMem<TC>& M) {
   using T = Tile2D<EQ, TX, TY>;
   static_assert(sizeof(TS) == sizeof(TC), "derivative coefficients are staged as stored");
-  constexpr int N0 = T::NV * T::R2, N1 = T::NS * T::R1;
+  constexpr int C1 = T::NT / T::R1X, C0 = T::NT / T::R2X;
+  static_assert(C1 >= 1 && C1 <= T::R1Y && C0 >= 1 && C0 <= T::R2Y,
+                "a pass of rows advances by at most one variable");
   const size_t ncell = (size_t)A.ncell;
-  for (int e = threadIdx.x; e < N1; e += T::NT) {
-    int v = e / T::R1, r = e - v * T::R1;
-    int ry = r / T::R1X, rx = r - ry * T::R1X;
-    cp_async_elem<sizeof(TS)>(&M.sl[e], &A.in.sl[v * ncell + M.gy[ry + 1] + M.gx[rx + 1]]);
-  }
-  if constexpr (sizeof(TC) == 8) {
-    for (int e = threadIdx.x; e < N0; e += T::NT) {
-      int v = e / T::R2, r = e - v * T::R2;
-      int ry = r / T::R2X, rx = r - ry * T::R2X;
-      cp_async_elem<8>(&M.c0[e], &A.in.c0[v * ncell + M.gy[ry] + M.gx[rx]]);
-    }
-  } else {
-    constexpr int I0 = (N0 + T::NT - 1) / T::NT, CH = 8;  // loads in flight per chunk
-#pragma unroll
-    for (int i0 = 0; i0 < I0; i0 += CH) {
-      double a[CH];
-#pragma unroll
-      for (int i = 0; i < CH; ++i) {
-        const int e = threadIdx.x + (i0 + i) * T::NT;
-        if (i0 + i < I0 && e < N0) {
-          int v = e / T::R2, r = e - v * T::R2;
-          int ry = r / T::R2X, rx = r - ry * T::R2X;
-          a[i] = __ldg(&A.in.c0[v * ncell + M.gy[ry] + M.gx[rx]]);
-        }
+  const int tid = threadIdx.x;
+  {  // derivative coefficients: rows (v, ry) of the halo-1 region
+    const int rx = tid % T::R1X, row0 = tid / T::R1X;
+    if (row0 < C1) {
+      const TS* src = A.in.sl + M.gx[rx + 1];
+      size_t voff = 0;
+      int ry = row0;
+      for (int row = row0; row < T::NS * T::R1Y; row += C1) {
+        cp_async_elem<sizeof(TS)>(&M.sl[row * T::R1X + rx], src + voff + M.gy[ry + 1]);
+        ry += C1;
+        if (ry >= T::R1Y) { ry -= T::R1Y; voff += ncell; }
       }
+    }
+  }
+  {  // averages: rows (v, ry) of the halo-2 region
+    constexpr int ROWS = T::NV * T::R2Y, P = (ROWS + C0 - 1) / C0, CH = 8;
+    const int rx = tid % T::R2X, row0 = tid / T::R2X;
+    if (row0 < C0) {
+      const double* src = A.in.c0 + M.gx[rx];
+      TC* dst = M.c0 + row0 * T::R2X + rx;
+      size_t voff = 0;
+      int ry = row0;
+      if constexpr (sizeof(TC) == 8) {
+        for (int p = 0; p < P && row0 + p * C0 < ROWS; ++p) {
+          cp_async_elem<8>(dst + p * C0 * T::R2X, src + voff + M.gy[ry]);
+          ry += C0;
+          if (ry >= T::R2Y) { ry -= T::R2Y; voff += ncell; }
+        }
+      } else {
 #pragma unroll
-      for (int i = 0; i < CH; ++i) {
-        const int e = threadIdx.x + (i0 + i) * T::NT;
-        if (i0 + i < I0 && e < N0) M.c0[e] = Cvt<TC>::to_tc(a[i]);
+        for (int p0 = 0; p0 < P; p0 += CH) {
+          double a[CH];
+#pragma unroll
+          for (int i = 0; i < CH; ++i) {
+            if (p0 + i < P && row0 + (p0 + i) * C0 < ROWS) {
+              a[i] = __ldg(src + voff + M.gy[ry]);
+              ry += C0;
+              if (ry >= T::R2Y) { ry -= T::R2Y; voff += ncell; }
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < CH; ++i)
+            if (p0 + i < P && row0 + (p0 + i) * C0 < ROWS)
+              dst[(p0 + i) * C0 * T::R2X] = Cvt<TC>::to_tc(a[i]);
+        }
       }
     }
   }
