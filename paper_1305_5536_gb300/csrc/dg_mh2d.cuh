@@ -219,20 +219,17 @@ __device__ __forceinline__ void prim_flux2d(const Gas<TC>& G, const TC* W, TC* F
 template <int EQ, class TC>
 __device__ __forceinline__ void face_flux_prim2d(const Gas<TC>& G, int dir, const TC* WL,
                                                  const TC* WR, TC* F, unsigned& err) {
+  // normal and transverse components picked with selects: one inlined solver
+  const bool xd = dir == 0;
+  const TC unl = xd ? WL[1] : WL[2], utl = xd ? WL[2] : WL[1];
+  const TC unr = xd ? WR[1] : WR[2], utr = xd ? WR[2] : WR[1];
   TC Ff[5];
   if (EQ == 0) {
-    if (dir == 0) exact_flux<TC, 1>(G, WL[0], WL[1], WL[3], &WL[2], WR[0], WR[1], WR[3], &WR[2], Ff, err);
-    else exact_flux<TC, 1>(G, WL[0], WL[2], WL[3], &WL[1], WR[0], WR[2], WR[3], &WR[1], Ff, err);
+    exact_flux<TC, 1>(G, WL[0], unl, WL[3], &utl, WR[0], unr, WR[3], &utr, Ff, err);
   } else {
-    if (dir == 0) {
-      const TC bn = TC(0.5) * (WL[4] + WR[4]);
-      hlld_flux<TC>(G, WL[0], WL[1], WL[2], WL[3], WL[5], WR[0], WR[1], WR[2], WR[3], WR[5], bn,
-                    Ff, err);
-    } else {
-      const TC bn = TC(0.5) * (WL[5] + WR[5]);
-      hlld_flux<TC>(G, WL[0], WL[2], WL[1], WL[3], WL[4], WR[0], WR[2], WR[1], WR[3], WR[4], bn,
-                    Ff, err);
-    }
+    const TC bn = TC(0.5) * (xd ? WL[4] + WR[4] : WL[5] + WR[5]);
+    hlld_flux<TC>(G, WL[0], unl, utl, WL[3], xd ? WL[5] : WL[4], WR[0], unr, utr, WR[3],
+                  xd ? WR[5] : WR[4], bn, Ff, err);
     F[4] = Ff[4];
   }
   F[0] = Ff[0];

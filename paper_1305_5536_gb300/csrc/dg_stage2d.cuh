@@ -225,18 +225,18 @@ __device__ __forceinline__ void face_flux2d(const Gas<TC>& G, int dir, const TC*
   }
   TC pl = G.gm1 * (cl[3] - TC(0.5) * (cl[1] * vxl + cl[2] * vyl) - magl);
   TC pr = G.gm1 * (cr[3] - TC(0.5) * (cr[1] * vxr + cr[2] * vyr) - magr);
+  // the face frame's normal and transverse components, picked with selects so
+  // that the solver is inlined once for both orientations
+  const bool xd = dir == 0;
+  const TC unl = xd ? vxl : vyl, utl = xd ? vyl : vxl;
+  const TC unr = xd ? vxr : vyr, utr = xd ? vyr : vxr;
   TC Ff[5];
   if (EQ == 0) {
-    if (dir == 0) exact_flux<TC, 1>(G, rl, vxl, pl, &vyl, rr, vxr, pr, &vyr, Ff, err);
-    else exact_flux<TC, 1>(G, rl, vyl, pl, &vxl, rr, vyr, pr, &vxr, Ff, err);
+    exact_flux<TC, 1>(G, rl, unl, pl, &utl, rr, unr, pr, &utr, Ff, err);
   } else {
-    if (dir == 0) {
-      TC bn = TC(0.5) * (cl[4] + cr[4]);
-      hlld_flux<TC>(G, rl, vxl, vyl, pl, cl[5], rr, vxr, vyr, pr, cr[5], bn, Ff, err);
-    } else {
-      TC bn = TC(0.5) * (cl[5] + cr[5]);
-      hlld_flux<TC>(G, rl, vyl, vxl, pl, cl[4], rr, vyr, vxr, pr, cr[4], bn, Ff, err);
-    }
+    const TC bn = TC(0.5) * (xd ? cl[4] + cr[4] : cl[5] + cr[5]);
+    hlld_flux<TC>(G, rl, unl, utl, pl, xd ? cl[5] : cl[4], rr, unr, utr, pr, xd ? cr[5] : cr[4],
+                  bn, Ff, err);
     F[4] = Ff[4];
   }
   F[0] = Ff[0];

@@ -196,12 +196,22 @@ __device__ __forceinline__ void stage3d_issue(const StateBuf<TS>& in, size_t nce
   constexpr int R1X = TX + 2, R1Y = TY + 2, R1 = R1X * R1Y * (TZ + 2);
   constexpr int NT = TX * TY * TZ;
   static_assert(sizeof(TS) == sizeof(TC), "derivative coefficients are staged as stored");
-  for (int e = threadIdx.x; e < NS * R1; e += NT) {
-    int v = e / R1, r = e - v * R1;
-    int rz = r / (R1X * R1Y), rr = r - rz * (R1X * R1Y);
-    int ry = rr / R1X, rx = rr - ry * R1X;
-    cp_async_elem<sizeof(TS)>(
-        &s_sl[e], &in.sl[v * ncell + (size_t)s_gz[rz + 1] + s_gy[ry + 1] + s_gx[rx + 1]]);
+  {  // planes (v, rz) of R1X x R1Y cells: thread t keeps position t % PL of every
+     // C1-th plane from plane t / PL on, so a copy costs one plane-offset lookup
+    constexpr int PL = R1X * R1Y, R1Z = TZ + 2, C1 = NT / PL;
+    static_assert(C1 >= 1 && C1 <= R1Z, "a pass of planes advances by at most one variable");
+    const int q = threadIdx.x % PL, p0 = threadIdx.x / PL;
+    if (p0 < C1) {
+      const int ry = q / R1X, rx = q - ry * R1X;
+      const TS* src = in.sl + s_gy[ry + 1] + s_gx[rx + 1];
+      size_t voff = 0;
+      int rz = p0;
+      for (int p = p0; p < NS * R1Z; p += C1) {
+        cp_async_elem<sizeof(TS)>(&s_sl[p * PL + q], src + voff + s_gz[rz + 1]);
+        rz += C1;
+        if (rz >= R1Z) { rz -= R1Z; voff += ncell; }
+      }
+    }
   }
   for (int r = threadIdx.x; r < R2; r += NT) {
     int rz = r / (R2X * R2Y), rr = r - rz * (R2X * R2Y);
