@@ -655,12 +655,15 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
   stage2d_compute<EQ, TC, TS, TX, TY, STAGE>(A, i0, j0, nblk, M, S);
 }
 
-// FP32: as many resident CTAs as 72 registers a thread allow (7 of 128 threads):
-// the stage kernels are latency bound.  FP64 keeps its registers (it would spill).
+// FP32: as many resident CTAs as 72 registers a thread allow for 128-thread
+// tiles (7 CTAs) and 64 for 256-thread tiles (4 CTAs, which their shared memory
+// also allows; measured +3 % over 80 registers and 3 CTAs despite 16-80 bytes of
+// spills): the stage kernels are issue and latency bound.  FP64 keeps its
+// registers (it would spill).
 template <int NT, class TC>
 struct StageMinBlocks {
-  static constexpr int v =
-      sizeof(TC) == 4 && 65536 / (72 * NT) > 0 ? 65536 / (72 * NT) : 1;
+  static constexpr int R = NT >= 256 ? 64 : 72;
+  static constexpr int v = sizeof(TC) == 4 && 65536 / (R * NT) > 0 ? 65536 / (R * NT) : 1;
 };
 
 template <int EQ, class TC, class TS, int TX, int TY, int STAGE>
