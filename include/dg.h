@@ -117,12 +117,15 @@ void dg_destroy(dg_ctx* ctx);
 const char* dg_last_error(const dg_ctx* ctx);
 
 /* Copy a state in (interchange layout, float64).  on_device != 0: `coeffs` is a
- * device pointer, else host memory.  Resets time and step counters, clears the
- * device error word and computes the first Courant time step.  Synchronises the
- * stream. */
+ * device pointer, else host memory (page-locked host memory is read in place by
+ * the layout kernels; pageable memory is staged plane by plane).  Resets time and
+ * step counters, clears the device error word and computes the first Courant
+ * time step.  Synchronises the stream. */
 dg_status dg_set_state(dg_ctx* ctx, const double* coeffs, int on_device);
 
-/* Copy the current state out (interchange layout, float64).  Synchronises. */
+/* Copy the current state out (interchange layout, float64; page-locked host
+ * memory is written in place, pageable memory through device staging).
+ * Synchronises. */
 dg_status dg_get_state(dg_ctx* ctx, double* coeffs, int on_device);
 
 /* Advance `nsteps` steps of the configured integrator.  dt_override > 0: every

@@ -546,8 +546,27 @@ dg_status autotune(dg_ctx* c) {
   return reset_ctl_and_cfl(c);
 }
 
+// Device address of page-locked (pinned or registered) host memory, or null for
+// pageable memory.  The layout kernels read and write such memory in place (over
+// NVLink-C2C on Grace-Blackwell), so a state crosses the link once, without the
+// per-plane staging copies through device scratch that pageable memory needs.
+static void* mapped_view(const void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 template <class TS>
 static dg_status set_state_t(dg_ctx* c, const double* src, int on_device) {
+  if (!on_device) {
+    if (const double* view = static_cast<const double*>(mapped_view(src))) {
+      src = view;
+      on_device = 1;
+    }
+  }
   for (const Prob& p : c->probs) {
     StateBuf<TS> dst = sbuf<TS>(c, c->cur, p);
     for (int k = 0; k < c->nplanes; ++k) {
@@ -566,6 +585,12 @@ static dg_status set_state_t(dg_ctx* c, const double* src, int on_device) {
 
 template <class TS>
 static dg_status get_state_t(dg_ctx* c, double* dst, int on_device) {
+  if (!on_device) {
+    if (double* view = static_cast<double*>(mapped_view(dst))) {
+      dst = view;
+      on_device = 1;
+    }
+  }
   for (const Prob& p : c->probs) {
     StateBuf<TS> src = sbuf<TS>(c, c->cur, p);
     for (int k = 0; k < c->nplanes; ++k) {
