@@ -569,6 +569,10 @@ static dg_status set_state_t(dg_ctx* c, const double* src, int on_device) {
   }
   for (const Prob& p : c->probs) {
     StateBuf<TS> dst = sbuf<TS>(c, c->cur, p);
+    if (on_device) {
+      CK(c, launch_state_in<TS>(src + p.plane_off, dst, c->pmap, p.ncell, c->stream));
+      continue;
+    }
     for (int k = 0; k < c->nplanes; ++k) {
       const double* plane = src + p.plane_off + (size_t)k * p.ncell;
       const double* dsrc = plane;
@@ -593,6 +597,10 @@ static dg_status get_state_t(dg_ctx* c, double* dst, int on_device) {
   }
   for (const Prob& p : c->probs) {
     StateBuf<TS> src = sbuf<TS>(c, c->cur, p);
+    if (on_device) {
+      CK(c, launch_state_out<TS>(src, dst + p.plane_off, c->pmap, p.ncell, c->stream));
+      continue;
+    }
     for (int k = 0; k < c->nplanes; ++k) {
       double* plane = dst + p.plane_off + (size_t)k * p.ncell;
       double* ddst = on_device ? plane : c->scratch;

@@ -55,6 +55,15 @@ cudaError_t launch_mh3m(int variant, int face_points, const Stage3DArgs<double>&
 cudaError_t launch_mh3m(int variant, int face_points, const Stage3DArgs<float>& a,
                         cudaStream_t st);
 
+// Layout conversion of all interchange planes of one problem (device or
+// page-locked host memory) to/from the state, in one launch.
+template <class TS>
+cudaError_t launch_state_in(const double* src, StateBuf<TS> dst, const PlaneMap& map, long ncell,
+                            cudaStream_t st);
+template <class TS>
+cudaError_t launch_state_out(StateBuf<TS> src, double* dst, const PlaneMap& map, long ncell,
+                             cudaStream_t st);
+
 // Layout conversion of one interchange plane (ncell doubles) to/from the state.
 template <class TS>
 cudaError_t launch_plane_in(const double* src, StateBuf<TS> dst, int kind, int idx, long ncell,

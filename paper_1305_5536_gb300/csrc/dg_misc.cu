@@ -48,6 +48,61 @@ cudaError_t launch_plane_out(StateBuf<TS> src, double* dst, int kind, int idx, l
   plane_out_kernel<TS><<<grid_for(ncell, 256), 256, 0, st>>>(src, dst, kind, idx, ncell);
   return cudaGetLastError();
 }
+// All planes of one problem in one launch (blockIdx.y = plane): the interchange
+// planes at src (device or page-locked host memory) into the state, or back.
+template <class TS>
+__global__ void state_in_kernel(const double* __restrict__ src, StateBuf<TS> dst, PlaneMap map,
+                                long ncell) {
+  const int k = blockIdx.y, kind = map.kind[k];
+  const size_t o = (size_t)map.idx[k] * ncell;
+  const double* s = src + (size_t)k * ncell;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < ncell;
+       i += (long)gridDim.x * blockDim.x) {
+    const double v = s[i];
+    if (kind == 0) dst.c0[o + i] = v;
+    else dst.sl[o + i] = (TS)v;
+  }
+}
+
+template <class TS>
+__global__ void state_out_kernel(StateBuf<TS> src, double* __restrict__ dst, PlaneMap map,
+                                 long ncell) {
+  const int k = blockIdx.y, kind = map.kind[k];
+  const size_t o = (size_t)map.idx[k] * ncell;
+  double* d = dst + (size_t)k * ncell;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < ncell;
+       i += (long)gridDim.x * blockDim.x)
+    d[i] = kind == 0 ? src.c0[o + i] : (double)src.sl[o + i];
+}
+
+static inline dim3 state_grid(long ncell, int nplanes) {
+  long b = (ncell + 255) / 256, cap = 152L * 16 / (nplanes > 0 ? nplanes : 1);
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return dim3((unsigned)b, (unsigned)nplanes);
+}
+
+template <class TS>
+cudaError_t launch_state_in(const double* src, StateBuf<TS> dst, const PlaneMap& map, long ncell,
+                            cudaStream_t st) {
+  state_in_kernel<TS><<<state_grid(ncell, map.nplanes), 256, 0, st>>>(src, dst, map, ncell);
+  return cudaGetLastError();
+}
+template <class TS>
+cudaError_t launch_state_out(StateBuf<TS> src, double* dst, const PlaneMap& map, long ncell,
+                             cudaStream_t st) {
+  state_out_kernel<TS><<<state_grid(ncell, map.nplanes), 256, 0, st>>>(src, dst, map, ncell);
+  return cudaGetLastError();
+}
+template cudaError_t launch_state_in<double>(const double*, StateBuf<double>, const PlaneMap&,
+                                             long, cudaStream_t);
+template cudaError_t launch_state_in<float>(const double*, StateBuf<float>, const PlaneMap&, long,
+                                            cudaStream_t);
+template cudaError_t launch_state_out<double>(StateBuf<double>, double*, const PlaneMap&, long,
+                                              cudaStream_t);
+template cudaError_t launch_state_out<float>(StateBuf<float>, double*, const PlaneMap&, long,
+                                             cudaStream_t);
+
 template cudaError_t launch_plane_in<double>(const double*, StateBuf<double>, int, int, long,
                                              cudaStream_t);
 template cudaError_t launch_plane_in<float>(const double*, StateBuf<float>, int, int, long,
