@@ -12,24 +12,31 @@
 
 namespace dgk {
 
-template <int EQ, class TC, class TS, int TX, int TY>
-static cudaError_t launch2d(int stage, const Stage2DArgs<TS>& a, cudaStream_t st) {
+template <int EQ, class TC, class TS, int TX, int TY, bool WENO>
+static cudaError_t launch2d_w(int stage, const Stage2DArgs<TS>& a, cudaStream_t st) {
   constexpr size_t smem = stage2d_smem_bytes<EQ, TX, TY, TC>();
   static_assert(smem <= 227 * 1024, "tile too large for shared memory");
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e1 = cudaFuncSetAttribute(stage2d_kernel<EQ, TC, TS, TX, TY, 1>,
+    cudaError_t e1 = cudaFuncSetAttribute(stage2d_kernel<EQ, TC, TS, TX, TY, 1, WENO>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaError_t e2 = cudaFuncSetAttribute(stage2d_kernel<EQ, TC, TS, TX, TY, 2>,
+    cudaError_t e2 = cudaFuncSetAttribute(stage2d_kernel<EQ, TC, TS, TX, TY, 2, WENO>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e1 != cudaSuccess) return e1;
     if (e2 != cudaSuccess) return e2;
     attr_set = true;
   }
   dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
-  if (stage == 1) stage2d_kernel<EQ, TC, TS, TX, TY, 1><<<grid, TX * TY, smem, st>>>(a);
-  else stage2d_kernel<EQ, TC, TS, TX, TY, 2><<<grid, TX * TY, smem, st>>>(a);
+  if (stage == 1) stage2d_kernel<EQ, TC, TS, TX, TY, 1, WENO><<<grid, TX * TY, smem, st>>>(a);
+  else stage2d_kernel<EQ, TC, TS, TX, TY, 2, WENO><<<grid, TX * TY, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+// The WENO-type limiter only in the instantiation that needs it.
+template <int EQ, class TC, class TS, int TX, int TY>
+static cudaError_t launch2d(int stage, const Stage2DArgs<TS>& a, cudaStream_t st) {
+  if (a.limiter == 2) return launch2d_w<EQ, TC, TS, TX, TY, true>(stage, a, st);
+  return launch2d_w<EQ, TC, TS, TX, TY, false>(stage, a, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -413,7 +413,9 @@ __device__ __forceinline__ void courant_commit2d(const Stage2DArgs<TS>& A, const
 // The rest of a tile once it is staged: primitives, limiter, faces, per-cell
 // right-hand side and Runge-Kutta combination; `nblk` is the number of tiles of
 // the problem (the last of them to finish stage 2 publishes the Courant speed).
-template <int EQ, class TC, class TS, int TX, int TY, int STAGE>
+// WENO = false compiles the WENO-type limiter out (for launches with limiter 0
+// or 1: its code raises the registers and stack of the common path).
+template <int EQ, class TC, class TS, int TX, int TY, int STAGE, bool WENO = true>
 __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0, int j0,
                                                 unsigned nblk, const TileMem<TC>& M,
                                                 TileScalars<TX * TY>& S) {
@@ -470,7 +472,7 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
       }
 #pragma unroll
       for (int k = 0; k < NS; ++k) s[k] = s_sl[k * R1 + r1];
-      if (A.limiter == 2) weno_cell2d<EQ, TC>(G, hh, W, Wn, s, nullptr);
+      if (WENO && A.limiter == 2) weno_cell2d<EQ, TC>(G, hh, W, Wn, s, nullptr);
       else limit_cell2d<EQ, TC>(G, hh, W, Wn, s);
 #pragma unroll
       for (int k = 0; k < NS; ++k) s_sl[k * R1 + r1] = s[k];
@@ -589,9 +591,7 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
     }
   } else {
     // V^{n+1} = 1/2 U^n + 1/2 (U^1 + dt L(U^1)), U^n = limited V^n of this cell
-    TC cn[NV], sn[NS];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) cn[v] = Cvt<TC>::to_tc(A.base.c0[v * ncell + gc]);
+    TC sn[NS];
     if (A.limiter && A.lim_sl) {
       // limited by stage 1 of this step
 #pragma unroll
@@ -601,7 +601,9 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
       for (int k = 0; k < NS; ++k) sn[k] = (TC)A.base.sl[k * ncell + gc];
     }
     if (A.limiter && !A.lim_sl) {
-      TC W[NP], Wn[4][NP];
+      TC cn[NV], W[NP], Wn[4][NP];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) cn[v] = Cvt<TC>::to_tc(A.base.c0[v * ncell + gc]);
       prims2d<EQ, TC>(G, cn, W, err);
       const size_t nb[4] = {(size_t)s_gy[ly + 2] + s_gx[lx + 1], (size_t)s_gy[ly + 2] + s_gx[lx + 3],
                             (size_t)s_gy[ly + 1] + s_gx[lx + 2], (size_t)s_gy[ly + 3] + s_gx[lx + 2]};
@@ -612,7 +614,7 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
         for (int v = 0; v < NV; ++v) c[v] = Cvt<TC>::to_tc(A.base.c0[v * ncell + nb[k]]);
         prims2d<EQ, TC>(G, c, Wn[k], err);
       }
-      if (A.limiter == 2) weno_cell2d<EQ, TC>(G, hh, W, Wn, sn, nullptr);
+      if (WENO && A.limiter == 2) weno_cell2d<EQ, TC>(G, hh, W, Wn, sn, nullptr);
       else limit_cell2d<EQ, TC>(G, hh, W, Wn, sn);
     }
 #pragma unroll
@@ -642,7 +644,7 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
 
 // One tile of one stage (classic staging): the CTA owns cells [i0, i0+TX) x
 // [j0, j0+TY) of the problem described by A.
-template <int EQ, class TC, class TS, int TX, int TY, int STAGE>
+template <int EQ, class TC, class TS, int TX, int TY, int STAGE, bool WENO = true>
 __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, int j0,
                                              unsigned nblk, unsigned char* smem_raw) {
   __shared__ TileScalars<TX * TY> S;
@@ -652,7 +654,7 @@ __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, i
   if (STAGE == 2) stage2d_prefetch_base<EQ, TC, TS, TX, TY>(A, M);
   stage2d_load<EQ, TC, TS, TX, TY>(A, M);
   __syncthreads();
-  stage2d_compute<EQ, TC, TS, TX, TY, STAGE>(A, i0, j0, nblk, M, S);
+  stage2d_compute<EQ, TC, TS, TX, TY, STAGE, WENO>(A, i0, j0, nblk, M, S);
 }
 
 // FP32: as many resident CTAs as 72 registers a thread allow for 128-thread
@@ -666,11 +668,11 @@ struct StageMinBlocks {
   static constexpr int v = sizeof(TC) == 4 && 65536 / (R * NT) > 0 ? 65536 / (R * NT) : 1;
 };
 
-template <int EQ, class TC, class TS, int TX, int TY, int STAGE>
+template <int EQ, class TC, class TS, int TX, int TY, int STAGE, bool WENO>
 __global__ void __launch_bounds__(TX * TY, (StageMinBlocks<TX * TY, TC>::v))
     stage2d_kernel(const Stage2DArgs<TS> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  stage2d_tile<EQ, TC, TS, TX, TY, STAGE>(A, blockIdx.x * TX, blockIdx.y * TY,
+  stage2d_tile<EQ, TC, TS, TX, TY, STAGE, WENO>(A, blockIdx.x * TX, blockIdx.y * TY,
                                           gridDim.x * gridDim.y, smem_raw);
 }
 
