@@ -6,24 +6,31 @@
 
 namespace dgk {
 
-template <class TC, class TS, int TX, int TY, int TZ>
-static cudaError_t launch3d(int stage, const Stage3DArgs<TS>& a, cudaStream_t st) {
+template <class TC, class TS, int TX, int TY, int TZ, bool WENO>
+static cudaError_t launch3d_w(int stage, const Stage3DArgs<TS>& a, cudaStream_t st) {
   constexpr size_t smem = stage3d_smem_bytes<TX, TY, TZ, TC>();
   static_assert(smem <= 227 * 1024, "tile too large for shared memory");
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e1 = cudaFuncSetAttribute(stage3d_kernel<TC, TS, TX, TY, TZ, 1>,
+    cudaError_t e1 = cudaFuncSetAttribute(stage3d_kernel<TC, TS, TX, TY, TZ, 1, WENO>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaError_t e2 = cudaFuncSetAttribute(stage3d_kernel<TC, TS, TX, TY, TZ, 2>,
+    cudaError_t e2 = cudaFuncSetAttribute(stage3d_kernel<TC, TS, TX, TY, TZ, 2, WENO>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e1 != cudaSuccess) return e1;
     if (e2 != cudaSuccess) return e2;
     attr_set = true;
   }
   dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + TZ - 1) / TZ);
-  if (stage == 1) stage3d_kernel<TC, TS, TX, TY, TZ, 1><<<grid, TX * TY * TZ, smem, st>>>(a);
-  else stage3d_kernel<TC, TS, TX, TY, TZ, 2><<<grid, TX * TY * TZ, smem, st>>>(a);
+  if (stage == 1) stage3d_kernel<TC, TS, TX, TY, TZ, 1, WENO><<<grid, TX * TY * TZ, smem, st>>>(a);
+  else stage3d_kernel<TC, TS, TX, TY, TZ, 2, WENO><<<grid, TX * TY * TZ, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+// The WENO-type limiter only in the instantiation that needs it.
+template <class TC, class TS, int TX, int TY, int TZ>
+static cudaError_t launch3d(int stage, const Stage3DArgs<TS>& a, cudaStream_t st) {
+  if (a.limiter == 2) return launch3d_w<TC, TS, TX, TY, TZ, true>(stage, a, st);
+  return launch3d_w<TC, TS, TX, TY, TZ, false>(stage, a, st);
 }
 
 int stage3d_variants(int) { return 2; }

@@ -244,7 +244,8 @@ struct Stage3dMinBlocks {
   static constexpr int v = sizeof(TC) == 4 && 65536 / (80 * NT) > 0 ? 65536 / (80 * NT) : 1;
 };
 
-template <class TC, class TS, int TX, int TY, int TZ, int STAGE>
+// WENO = false compiles the WENO-type limiter out (launches with limiter 0 or 1).
+template <class TC, class TS, int TX, int TY, int TZ, int STAGE, bool WENO>
 __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, TC>::v))
     stage3d_kernel(const Stage3DArgs<TS> A) {
   constexpr int R2X = TX + 4, R2Y = TY + 4, R2Z = TZ + 4, R2 = R2X * R2Y * R2Z;
@@ -330,7 +331,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
       }
 #pragma unroll
       for (int k = 0; k < 15; ++k) s[k] = s_sl[k * R1 + r1];
-      if (A.limiter == 2) weno_cell3d<TC>(G, hh, W, Wn, s, nullptr);
+      if (WENO && A.limiter == 2) weno_cell3d<TC>(G, hh, W, Wn, s, nullptr);
       else limit_cell3d<TC>(G, hh, W, Wn, s);
 #pragma unroll
       for (int k = 0; k < 15; ++k) s_sl[k * R1 + r1] = s[k];
@@ -464,7 +465,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
         for (int v = 0; v < 5; ++v) c[v] = Cvt<TC>::to_tc(A.base.c0[v * ncell + nb[k]]);
         prims3d<TC>(G, c, Wn[k], err);
       }
-      if (A.limiter == 2) weno_cell3d<TC>(G, hh, W, Wn, sn, nullptr);
+      if (WENO && A.limiter == 2) weno_cell3d<TC>(G, hh, W, Wn, sn, nullptr);
       else limit_cell3d<TC>(G, hh, W, Wn, sn);
     }
 #pragma unroll
