@@ -8,10 +8,13 @@
 //   * Sec. 2.2  eq. `dg`        weak form, Taylor basis (1, x, y[, z]) about the
 //                               centroid, eqs. `fv`, `dgderiv`, `fv3d`,
 //                               `dgderiv3d`, mass matrix M, locally
-//                               divergence-free 2D magnetic basis V1..V5
-//   * Sec. 2.3                  exact Riemann solver (Euler), HLLD (MHD)
+//                               divergence-free magnetic bases V1..V5 (2D)
+//                               and V1..V11 (3D)
+//   * Sec. 2.3                  exact Riemann solver (Euler), HLLD (MHD; two
+//                               transverse components in 3D)
 //   * Sec. 2.5                  min/max slope limiter on primitive variables, and
-//                               the WENO-type limiter (limiter = 2)
+//                               the WENO-type limiter (limiter = 2; the field's
+//                               stencil gradient L2-projected onto the basis)
 //   * Sec. 2.6                  averaged normal B at faces; Stokes div-B estimate
 // The time integrator is the two-stage strong-stability-preserving Runge-Kutta
 // method (the "traditional DG" integrator named in Sec. 2.4) and faces are
