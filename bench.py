@@ -13,7 +13,9 @@ step sooner) the solver restarts from the initial state, which stays resident on
 the device; the restart lies outside the timed events.  Kernel durations come from
 CUDA events the library records around each stage-kernel launch.  Multi-GPU
 (--gpus N under torchrun): independent replicas, one per rank (weak scaling),
-barrier + max over ranks.  ``--impl reference`` times the CPU oracle instead.
+barrier + max over ranks.  The default workload's line also carries the adjoint
+step time (the checkpointed adjoint of 100 steps of a 2D Euler 256^2 problem,
+FP64 and FP32).  ``--impl reference`` times the CPU oracle instead.
 """
 import argparse
 import hashlib
@@ -309,6 +311,42 @@ def run_gpu(args):
         s.close()
         return res
 
+    def measure_adjoint(prec):
+        """The adjoint workload: 2D Euler 256^2, a seeded Gaussian random density on
+        the smooth-wave background, 100 SSP-RK2 steps recorded with checkpoints
+        every 10 (limiter off), objective 1/2 int (rho_h - rho_target)^2 exact on
+        P1; its gradient with respect to the initial coefficients by the
+        checkpointed adjoint (recomputation of each segment, reverse sweep).
+        Forward and adjoint timed with CUDA events on the solver's stream."""
+        n, K = (256, 256), 100
+        u0 = torch.from_numpy(ics.euler2d_random_density(n)[0]).cuda()
+        tgt = torch.from_numpy(ics.euler2d_random_density(n, seed=99)[0][0:3]).cuda()
+        hx, hy = 1.0 / n[0], 1.0 / n[1]
+        w = torch.tensor([1.0, hx * hx / 12, hy * hy / 12], dtype=torch.float64,
+                         device="cuda").view(3, 1, 1) * (hx * hy)
+        s = dg.DGSolver("euler", 2, n, precision=prec, limiter=0, cfl=0.3, ckpt_every=10)
+        res = None
+        for _ in range(2):  # the first run warms the graphs and the autotuner
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            s.set_state(u0)
+            ev[0].record(stream)
+            s.record(K)
+            ev[1].record(stream)
+            uT = s.get_state(device="cuda")
+            g = torch.zeros_like(uT)
+            g[0:3] = w * (uT[0:3] - tgt)
+            ev[2].record(stream)
+            g0 = s.adjoint(g)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            f_ms, a_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+            res = {"forward_ms": f_ms, "adjoint_ms": a_ms, "adjoint_ms_per_step": a_ms / K,
+                   "adjoint_over_forward": a_ms / f_ms,
+                   "adjoint_cell_steps_per_s": K * n[0] * n[1] / (a_ms * 1e-3),
+                   "grad_norm": float(g0.norm())}
+        s.close()
+        return res
+
     r32 = measure("fp32", args.steps, args.warmup, True)
     r64 = measure("fp64", max(3, min(args.steps, 20)), max(3, args.warmup), False)
     if rank != 0:
@@ -361,6 +399,12 @@ def run_gpu(args):
         "gpu_launches": int(sum(r32["kernel_launches"])),
         "clocks": r32["clocks"],
     }
+    if args.workload == "orszag_tang_512" and not args.no_adjoint:
+        out["adjoint"] = {
+            "workload": "2D Euler 256x256, seeded Gaussian random density (rms 0.05, "
+                        "correlation length 0.1), 100 SSP-RK2 steps at CFL 0.3, limiter off, "
+                        "checkpoint every 10 steps, objective 1/2 int (rho - rho_target)^2",
+            "fp64": measure_adjoint("fp64"), "fp32": measure_adjoint("fp32")}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, u0)
     print(json.dumps(out))
@@ -468,6 +512,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="orszag_tang_512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint timing of the default workload's line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
