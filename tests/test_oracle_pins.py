@@ -605,3 +605,248 @@ def test_tangent_matches_central_differences(lim):
     um, _ = P.step(u - eps * du, dt)
     fd = (up - um) / (2 * eps)
     np.testing.assert_allclose(dout, fd, atol=1e-7 * np.abs(fd).max())
+
+
+# ----------------------------------------------------------------------------
+# Courant time step (the configs' CFL rule; the paper gives none): on a uniform
+# state every cell has the same signal speed, so
+#   dt = CFL / sum_d (|v_d| + c_d) / dx_d
+# with c_d the sound speed sqrt(gamma p / rho) (Euler) or the fast magnetosonic
+# speed along d (MHD), written out here from its textbook definition
+#   c_f^2 = (a^2 + b^2 + sqrt((a^2 + b^2)^2 - 4 a^2 b_d^2)) / 2,
+#   a^2 = gamma p / rho, b^2 = |B|^2 / rho, b_d^2 = B_d^2 / rho.
+# ----------------------------------------------------------------------------
+
+def _uniform_state(P, W, g):
+    """Interchange state of a uniform primitive state W = (rho, v[dim], p[, B])."""
+    u = np.zeros(P.shape)
+    dim = P.dim
+    K = dim + 1
+    rho, v, p = W[0], list(W[1:1 + dim]), W[1 + dim]
+    B = list(W[2 + dim:]) if P.eq == O.MHD else []
+    E = p / (g - 1) + 0.5 * rho * sum(x * x for x in v) + 0.5 * sum(b * b for b in B)
+    u[0] = rho
+    for a in range(dim):
+        u[(1 + a) * K] = rho * v[a]
+    u[(1 + dim) * K] = E
+    for a, b in enumerate(B):
+        u[(2 + dim) * K + a] = b
+    return u
+
+
+def _fast(rho, p, B, d, g):
+    a2 = g * p / rho
+    b2 = sum(b * b for b in B) / rho
+    bd2 = B[d] * B[d] / rho
+    return math.sqrt(0.5 * (a2 + b2 + math.sqrt((a2 + b2) ** 2 - 4 * a2 * bd2)))
+
+
+def test_cfl_dt_closed_form_euler_2d_anisotropic():
+    g = 1.4
+    P = O.Problem(O.EULER, 2, (5, 7), box=(1.0, 2.1), gamma=g)
+    W = (1.3, 0.4, -0.7, 2.2)
+    u = _uniform_state(P, W, g)
+    c = math.sqrt(g * W[3] / W[0])
+    s = (abs(W[1]) + c) / P.h[0] + (abs(W[2]) + c) / P.h[1]
+    dt, fl = P.cfl_dt(u, cfl=0.37)
+    assert fl == 0
+    assert dt == pytest.approx(0.37 / s, rel=1e-14)
+    # the rule sums over directions: the largest single-direction rate would give
+    # a time step at least 1.5 times longer here
+    assert 0.37 / max((abs(W[1]) + c) / P.h[0], (abs(W[2]) + c) / P.h[1]) > 1.5 * dt
+
+
+def test_cfl_dt_closed_form_euler_3d_and_the_fastest_cell():
+    g = 5.0 / 3.0
+    P = O.Problem(O.EULER, 3, (4, 3, 5), box=(1.0, 0.6, 2.0), gamma=g)
+    W = (0.8, -0.3, 0.2, 0.5, 1.1)
+    u = _uniform_state(P, W, g)
+    c = math.sqrt(g * W[4] / W[0])
+    s = sum((abs(W[1 + a]) + c) / P.h[a] for a in range(3))
+    dt, fl = P.cfl_dt(u, cfl=0.3)
+    assert fl == 0
+    assert dt == pytest.approx(0.3 / s, rel=1e-14)
+    # one cell moving faster along z sets the step: max over cells
+    u2 = u.copy()
+    vz = 2.5
+    u2[12, 2, 1, 3] = W[0] * vz
+    u2[16, 2, 1, 3] = W[4] / (g - 1) + 0.5 * W[0] * (W[1] ** 2 + W[2] ** 2 + vz ** 2)
+    s2 = (abs(W[1]) + c) / P.h[0] + (abs(W[2]) + c) / P.h[1] + (vz + c) / P.h[2]
+    dt2, fl = P.cfl_dt(u2, cfl=0.3)
+    assert fl == 0
+    assert dt2 == pytest.approx(0.3 / s2, rel=1e-14)
+
+
+def test_cfl_dt_closed_form_mhd_fast_speed_per_direction():
+    g = 5.0 / 3.0
+    P = O.Problem(O.MHD, 2, (6, 4), box=(1.0, 0.5), gamma=g)
+    W = (1.2, 0.3, -0.15, 0.7, 1.4, -0.35)  # rho, vx, vy, p, Bx, By
+    u = _uniform_state(P, W, g)
+    rho, p, B = W[0], W[3], (W[4], W[5], 0.0)
+    cx, cy = _fast(rho, p, B, 0, g), _fast(rho, p, B, 1, g)
+    s = (abs(W[1]) + cx) / P.h[0] + (abs(W[2]) + cy) / P.h[1]
+    dt, fl = P.cfl_dt(u, cfl=0.3)
+    assert fl == 0
+    assert dt == pytest.approx(0.3 / s, rel=1e-14)
+    # the fast speeds along x and y differ from each other and from the sound speed,
+    # so the sound speed or one direction's fast speed for both would be caught
+    a = math.sqrt(g * p / rho)
+    for wrong in ((abs(W[1]) + a) / P.h[0] + (abs(W[2]) + a) / P.h[1],
+                  (abs(W[1]) + cx) / P.h[0] + (abs(W[2]) + cx) / P.h[1],
+                  (abs(W[1]) + cy) / P.h[0] + (abs(W[2]) + cy) / P.h[1]):
+        assert abs(0.3 / wrong - dt) > 1e-3 * dt
+
+
+# ----------------------------------------------------------------------------
+# Conservation totals: V * sum over cells of each conserved average, with
+# compensated summation.  Averages a_v(i, j[, k]) = (v + 1)(1 + i + 2j [+ 3k]) sum
+# to closed forms (arithmetic series); every derivative plane holds large values
+# that must not enter.
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("eq,dim", [(O.EULER, 2), (O.MHD, 2), (O.EULER, 3), (O.MHD, 3)])
+def test_totals_closed_form(eq, dim):
+    n = (5, 7) if dim == 2 else (3, 4, 5)
+    box = (1.0, 2.1) if dim == 2 else (1.0, 0.6, 2.0)
+    P = O.Problem(eq, dim, n, box=box)
+    u = np.full(P.shape, 1e6)  # derivative planes: must not enter the totals
+    nT = 4 if dim == 2 else 5
+    K = dim + 1
+    avg_planes = [v * K for v in range(nT)]
+    if eq == O.MHD:
+        avg_planes += [nT * K + a for a in range(dim)]  # b1, b2[, b3]
+    idx = np.indices(P.shape[1:])  # (k,) j, i
+    lin = 1.0 + idx[-1] + 2.0 * idx[-2] + (3.0 * idx[0] if dim == 3 else 0.0)
+    for v, pl in enumerate(avg_planes):
+        u[pl] = (v + 1) * lin
+    ncell = int(np.prod(n))
+    nx, ny = n[0], n[1]
+    nz = n[2] if dim == 3 else 1
+    # sum of (1 + i + 2 j + 3 k) over the grid
+    S = ncell + ny * nz * nx * (nx - 1) / 2 + 2 * nx * nz * ny * (ny - 1) / 2 + \
+        (3 * nx * ny * nz * (nz - 1) / 2 if dim == 3 else 0.0)
+    V = float(np.prod(P.h[:dim]))
+    got = P.totals(u)
+    assert got.size == len(avg_planes)
+    np.testing.assert_allclose(got, [(v + 1) * S * V for v in range(len(avg_planes))],
+                               rtol=1e-14)
+
+
+def test_totals_are_compensated():
+    """Averages alternating 1e16, 1, -1e16, 1 on a 4 x 4 grid: the exact total is
+    8 * V; plain left-to-right summation in FP64 loses every 1."""
+    P = O.Problem(O.EULER, 2, (4, 4), box=(2.0, 0.5))
+    u = np.zeros(P.shape)
+    pattern = np.array([1e16, 1.0, -1e16, 1.0] * 4).reshape(4, 4)
+    u[0] = pattern
+    u[9] = 1.0
+    plain = 0.0
+    for x in pattern.ravel():
+        plain += x
+    assert plain != 8.0
+    V = P.h[0] * P.h[1]
+    got = P.totals(u)
+    assert got[0] == 8.0 * V
+    assert got[3] == 16.0 * V
+
+
+# ----------------------------------------------------------------------------
+# Min/max limiter (Sec. 2.5): exact factor alpha = min(1, min_f psi_f) with
+#   psi_f = (phimax - phi)/dphi_f  (dphi_f > 0),
+#           (phimin - phi)/dphi_f  (dphi_f < 0),
+#           1                      (dphi_f = 0),
+#   dphi_f = grad phi . (face centroid - cell centroid),
+# on a hand-built stencil: density varies, velocity is zero and pressure uniform,
+# so the density slope of the centre cell is the only derivative coefficient.
+# ----------------------------------------------------------------------------
+
+def _rho_stencil(P, centre, nbrs, slope):
+    """Periodic 3 x 3 (2D) or 3 x 3 x 3 (3D) grid, rho = 1 except the centre cell
+    and its face neighbours; the centre's density slope along the given axis."""
+    g = P.gamma
+    u = _uniform_state(P, (1.0,) + (0.0,) * P.dim + (1.0,) + ((0.0, 0.0) if P.eq == O.MHD else ()), g)
+    c = (1,) * P.dim
+    u[(0,) + c] = centre
+    for (axis, side), rho in nbrs.items():
+        pos = list(c)
+        pos[P.dim - 1 - axis] += side  # arrays are [.., y, x]: axis 0 is the last index
+        u[(0,) + tuple(pos)] = rho
+    axis, gval = slope
+    u[(1 + axis,) + c] = gval
+    return u, c
+
+
+@pytest.mark.parametrize("dim,axis", [(2, 0), (2, 1), (3, 2)])
+@pytest.mark.parametrize("case", ["up", "down", "flat"])
+def test_minmax_limiter_alpha_exact(dim, axis, case):
+    box = (1.0, 0.6) if dim == 2 else (1.0, 0.6, 2.1)
+    n = (3,) * dim
+    P = O.Problem(O.EULER, dim, n, box=box, gamma=1.4, limiter=1)
+    h = P.h[axis]
+    gval = 0.4 / h  # face extrapolations dphi = +-0.2 along the axis, 0 across it
+    if case == "up":      # + face binds: psi = (1.1 - 1)/0.2 = 0.5; - face: (0.5 - 1)/-0.2 = 2.5
+        nb = {(axis, +1): 1.1, (axis, -1): 0.5}
+        alpha = 0.5
+    elif case == "down":  # - face binds: psi = (0.9 - 1)/-0.2 = 0.5; + face: (1.5 - 1)/0.2 = 2.5
+        nb = {(axis, +1): 1.5, (axis, -1): 0.9}
+        alpha = 0.5
+    else:                 # both psi = 2.5 and the faces across the axis have dphi = 0: alpha = 1
+        nb = {(axis, +1): 1.5, (axis, -1): 0.5}
+        alpha = 1.0
+    u, c = _rho_stencil(P, 1.0, nb, (axis, gval))
+    ul, fl = P.limit(u)
+    assert fl == 0
+    assert ul[(1 + axis,) + c] == pytest.approx(alpha * gval, rel=1e-14)
+    others = [k for k in range(P.shape[0]) if k % (dim + 1) != 0 and k != 1 + axis]
+    assert np.all(ul[others][(slice(None),) + c] == 0.0)
+
+
+def test_minmax_limiter_alpha_exact_two_directions():
+    """Gradients along x and y: phimax and phimin are taken over all four face
+    neighbours, alpha is the minimum over all four faces, and one alpha scales both
+    components."""
+    P = O.Problem(O.EULER, 2, (3, 3), box=(1.0, 0.6), gamma=1.4, limiter=1)
+    gx, gy = 0.1 / (0.5 * P.h[0]), 0.25 / (0.5 * P.h[1])  # dphi = +-0.1 (x), +-0.25 (y)
+    # phimax = 1.05 (x+), phimin = 0.7 (x-): psi = 0.05/0.1 = 0.5 (x+), -0.3/-0.1 = 3 (x-),
+    # 0.05/0.25 = 0.2 (y+), -0.3/-0.25 = 1.2 (y-)
+    u, c = _rho_stencil(P, 1.0, {(0, 1): 1.05, (0, -1): 0.7, (1, 1): 1.02, (1, -1): 0.9},
+                        (0, gx))
+    u[(2,) + c] = gy
+    ul, fl = P.limit(u)
+    assert fl == 0
+    assert ul[(1,) + c] == pytest.approx(0.2 * gx, rel=1e-14)
+    assert ul[(2,) + c] == pytest.approx(0.2 * gy, rel=1e-14)
+
+
+def test_minmax_limiter_shared_field_factor_exact():
+    """2D MHD: alpha_Bx = 0.5 (dBx/dx = a3 against an x neighbour), alpha_By = 0.8
+    (dBy/dx = a2): the shared field factor is min = 0.5 on (a1, a2, a3)."""
+    P = O.Problem(O.MHD, 2, (3, 3), box=(1.0, 0.6), gamma=5.0 / 3.0, limiter=1)
+    g = P.gamma
+    bx0, by0 = 0.3, -0.2
+    u = _uniform_state(P, (1.0, 0.0, 0.0, 1.0, bx0, by0), g)
+    c = (1, 1)
+    hx = 0.5 * P.h[0]
+    a3, a2 = 0.2 / hx, 0.1 / hx  # dBx at the x faces +-0.2, dBy at the x faces +-0.1
+    # dBx/dy = a1 = 0 and dBy/dy = -a3: y faces of By extrapolate by -+a3 h_y/2
+    u[16][c] = a3
+    u[15][c] = a2
+    # neighbour field averages: Bx: x+ 0.4 (psi 0.1/0.2 = 0.5), x- -0.2 (psi 2.5);
+    # By: x+ -0.12 (psi 0.08/0.1 = 0.8), x- -0.7 (psi 5); y neighbours of By far out
+    # (their psi is large), and the energy kept so that the pressure stays 1
+    def setB(pos, bx, by):
+        u[12][pos], u[13][pos] = bx, by
+        u[9][pos] = 1.0 / (g - 1) + 0.5 * (bx * bx + by * by)
+    setB((1, 2), 0.4, -0.12)
+    setB((1, 0), -0.2, -0.7)
+    setB((2, 1), bx0, 5.0)
+    setB((0, 1), bx0, -5.0)
+    setB(c, bx0, by0)
+    # the pressure slope from the field slopes: keep p uniform at the centroid
+    u[10][c] = bx0 * a3 + by0 * a2
+    u[11][c] = -by0 * a3
+    ul, fl = P.limit(u)
+    assert fl == 0
+    assert ul[16][c] == pytest.approx(0.5 * a3, rel=1e-13)
+    assert ul[15][c] == pytest.approx(0.5 * a2, rel=1e-13)
+    assert ul[14][c] == 0.0
