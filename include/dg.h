@@ -170,8 +170,17 @@ dg_status dg_adjoint_step(dg_ctx* ctx, const double* lam_next, double* lam_prev,
 
 /* Forward steps that record the trajectory for dg_adjoint: like dg_step, plus a
  * device checkpoint of the state every cfg.ckpt_every steps and the time step of
- * every step.  Recording restarts when the state is set. */
+ * every step.  Successive calls extend one recording.  Any other change of the
+ * state ends it: dg_set_state, or dg_step with nsteps > 0 (a later dg_record then
+ * starts a new recording from the state reached, and dg_adjoint returns
+ * DG_ESTATE until it does). */
 dg_status dg_record(dg_ctx* ctx, int nsteps, double dt_override, double* t_out);
+
+/* A counter that changes whenever the recorded trajectory changes (extended by
+ * dg_record, ended by dg_step or dg_set_state), so that a caller that keeps a
+ * recording for a later dg_adjoint can check that it is still the same one.
+ * -1 for a null context.  No device work. */
+long long dg_record_generation(const dg_ctx* ctx);
 
 /* Gradient of an objective of the final recorded state with respect to the
  * state at the start of the recording, by reverse sweeps over the recorded

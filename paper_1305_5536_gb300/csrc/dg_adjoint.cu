@@ -679,10 +679,15 @@ void adjoint_free(AdjointStore& s) {
   cudaFree(s.ckpt);
   cudaFree(s.dt_hist);
   cudaFree(s.work);
+  const long long gen = s.generation;
   s = AdjointStore();
+  s.generation = gen + 1;
 }
 
-void adjoint_reset(AdjointStore& s) { s.nrec = 0; }
+void adjoint_reset(AdjointStore& s) {
+  s.nrec = 0;
+  s.generation++;
+}
 
 dg_status adjoint_reserve(AdjointStore& s, int nplanes, long ncell, int k, long long nsteps,
                           std::string& msg) {

@@ -15,6 +15,9 @@ struct AdjointStore {
   double* dt_hist = nullptr;
   long long cap_steps = 0;
   long long nrec = 0;
+  // changes whenever the recorded trajectory does (a recording extended, ended or
+  // restarted), so that a caller holding a recording can tell that it is gone
+  long long generation = 0;
   size_t ckpt_elems = 0;
   long ncell = 0;
   int nplanes = 0;

@@ -84,7 +84,7 @@ __device__ __forceinline__ Stage2DArgs<TS> problem_args(const BatchArgs<TS>& B, 
   return a;
 }
 
-template <int EQ, class TC, class TS, int TX, int TY, int STAGE>
+template <int EQ, class TC, class TS, int TX, int TY, int STAGE, bool WENO>
 __device__ __forceinline__ void sweep(const BatchArgs<TS>& B, unsigned char* smem) {
   for (int t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
     const int ip = find_problem(B.probs, B.nprob, t);
@@ -93,25 +93,27 @@ __device__ __forceinline__ void sweep(const BatchArgs<TS>& B, unsigned char* sme
     const int ty = lt / p.tiles_x, tx = lt - ty * p.tiles_x;
     const Stage2DArgs<TS> a = problem_args(B, p, ip, STAGE);
     __syncthreads();  // the previous tile is done with shared memory
-    stage2d_tile<EQ, TC, TS, TX, TY, STAGE>(a, tx * TX, ty * TY, (unsigned)p.ntiles, smem);
+    stage2d_tile<EQ, TC, TS, TX, TY, STAGE, WENO>(a, tx * TX, ty * TY, (unsigned)p.ntiles, smem);
   }
 }
 
-template <int EQ, class TC, class TS, int TX, int TY>
+// WENO = false compiles the WENO-type limiter out (launches with limiter 0 or 1),
+// as in the single-problem stage kernels: the tile code is then the same.
+template <int EQ, class TC, class TS, int TX, int TY, bool WENO>
 __global__ void __launch_bounds__(TX * TY, (StageMinBlocks<TX * TY, TC>::v))
     batch2d_kernel(const BatchArgs<TS> B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  sweep<EQ, TC, TS, TX, TY, 1>(B, smem_raw);
+  sweep<EQ, TC, TS, TX, TY, 1, WENO>(B, smem_raw);
   if (!grid_barrier(B.bar, gridDim.x + B.barrier_extra, B.spin_limit)) {
     if (threadIdx.x == 0) atomicOr(&B.ctl[0].err, ERR_TIMEOUT);
   }
-  sweep<EQ, TC, TS, TX, TY, 2>(B, smem_raw);
+  sweep<EQ, TC, TS, TX, TY, 2, WENO>(B, smem_raw);
 }
 
-template <int EQ, class TC, class TS, int TX, int TY>
-cudaError_t launch_batch_t(const BatchArgs<TS>& B, cudaStream_t st, int* grid_out) {
+template <int EQ, class TC, class TS, int TX, int TY, bool WENO>
+cudaError_t launch_batch_w(const BatchArgs<TS>& B, cudaStream_t st, int* grid_out) {
   constexpr size_t smem = stage2d_smem_bytes<EQ, TX, TY, TC>();
-  auto kern = batch2d_kernel<EQ, TC, TS, TX, TY>;
+  auto kern = batch2d_kernel<EQ, TC, TS, TX, TY, WENO>;
   static int per_sm = -1, nsm = 0;
   if (per_sm < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -124,6 +126,7 @@ cudaError_t launch_batch_t(const BatchArgs<TS>& B, cudaStream_t st, int* grid_ou
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
   }
   int grid = per_sm * nsm;
+  if (B.max_ctas > 0 && grid > B.max_ctas) grid = B.max_ctas;
   if (grid > B.ntiles) grid = B.ntiles;
   if (grid_out) *grid_out = grid;
   cudaLaunchConfig_t cfg = {};
@@ -137,6 +140,12 @@ cudaError_t launch_batch_t(const BatchArgs<TS>& B, cudaStream_t st, int* grid_ou
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, B);
+}
+
+template <int EQ, class TC, class TS, int TX, int TY>
+cudaError_t launch_batch_t(const BatchArgs<TS>& B, cudaStream_t st, int* grid_out) {
+  if (B.limiter == 2) return launch_batch_w<EQ, TC, TS, TX, TY, true>(B, st, grid_out);
+  return launch_batch_w<EQ, TC, TS, TX, TY, false>(B, st, grid_out);
 }
 
 }  // namespace

@@ -34,6 +34,8 @@ struct BatchArgs {
   unsigned* bar;          // grid barrier: arrivals, generation
   long long spin_limit;   // polls before a barrier wait gives up
   int barrier_extra;      // expected arrivals beyond the grid (0; 1 in a timeout test)
+  int max_ctas = 0;       // largest grid (0: every resident CTA; a test hook sets it so
+                          // that each CTA walks many tiles)
 };
 
 cudaError_t launch_batch2d(int eq, int variant, const BatchArgs<double>& B, cudaStream_t st,

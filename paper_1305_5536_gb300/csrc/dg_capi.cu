@@ -77,6 +77,9 @@ struct dg_ctx {
   unsigned* bar = nullptr;
   long long spin_limit = 1LL << 24;
   int extra_arrivals = 0;
+  // test hook DG_TEST_MAX_CTAS: cap on the grids of the persistent (TMA, batched)
+  // kernels, so that every CTA processes many tiles
+  int max_ctas = 0;
   std::string kname;
 };
 
@@ -228,6 +231,7 @@ cudaError_t launch_batch_step_t(dg_ctx* c, int a, int b, double dtov) {
   B.bar = c->bar;
   B.spin_limit = c->spin_limit;
   B.barrier_extra = c->extra_arrivals;
+  B.max_ctas = c->max_ctas;
   return launch_batch2d(c->eq, v, B, c->launch_stream, nullptr);
 }
 
@@ -247,6 +251,7 @@ cudaError_t launch_stage_t(dg_ctx* c, int stage, int in, int base, int out, doub
       a.out = sbuf<TS>(c, out, p);
       a.lim_sl = lim >= 0 ? sbuf<TS>(c, lim, p).sl : nullptr;
       a.ctl = c->ctl + ip;
+      a.max_ctas = c->max_ctas;
       cudaError_t e = launch_stage2d(c->eq, c->variant < 0 ? 0 : c->variant, stage, a,
                                      c->launch_stream);
       if (e != cudaSuccess) return e;
@@ -702,6 +707,7 @@ static dg_status init_common(const dg_config* cfgs, int nprob, void* stream, dg_
   build_plane_map(c);
   c->stream = (cudaStream_t)stream;
   c->launch_stream = c->stream;
+  if (const char* cap = getenv("DG_TEST_MAX_CTAS")) c->max_ctas = std::max(0, atoi(cap));
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -794,6 +800,10 @@ dg_status dg_step(dg_ctx* c, int nsteps, double dt_override, double* t_out) {
   if (!c->state_set) return fail(c, DG_ESTATE, "no state has been set");
   if (nsteps < 0) return fail(c, DG_EINVAL, "nsteps must be >= 0");
   double dtov = dt_override > 0.0 ? dt_override : 0.0;
+  // steps outside dg_record end the recorded trajectory: a later dg_record starts
+  // a new one from the state these steps reach, and dg_adjoint has nothing to run
+  // back over until then
+  if (nsteps > 0) adjoint_reset(c->adj);
   int done = 0;
   if (!c->prof && nsteps >= 2) {
     cudaGraphExec_t ex;
@@ -992,6 +1002,7 @@ dg_status dg_record(dg_ctx* c, int nsteps, double dt_override, double* t_out) {
     std::swap(c->cur, c->nxt);
     c->adj.nrec++;
   }
+  if (nsteps > 0) c->adj.generation++;
   CK(c, cudaMemcpyAsync(&h, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   h.dt_hist = nullptr;
@@ -1001,6 +1012,8 @@ dg_status dg_record(dg_ctx* c, int nsteps, double dt_override, double* t_out) {
   if (t_out) *t_out = c->ctl_host[0].t;
   return e;
 }
+
+long long dg_record_generation(const dg_ctx* c) { return c ? c->adj.generation : -1; }
 
 dg_status dg_adjoint(dg_ctx* c, const double* lam_N, double* lam_0) {
   if (!c || !lam_N || !lam_0) return fail(c, DG_EINVAL, "null argument");

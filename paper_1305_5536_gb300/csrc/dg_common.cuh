@@ -64,6 +64,9 @@ struct Stage2DArgs {
   // own cell before overwriting it.  Null: stage 2 recomputes them.
   TS* lim_sl;
   Ctl* ctl;
+  // Largest grid of a persistent launch (the TMA kernels), 0 = as many CTAs as are
+  // resident.  Set only by a test hook, so that each CTA walks many tiles.
+  int max_ctas = 0;
 };
 
 // Arguments of one stage launch on one periodic 3D grid.

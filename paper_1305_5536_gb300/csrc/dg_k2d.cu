@@ -122,6 +122,7 @@ static cudaError_t launch2d_tma(int stage, const Stage2DArgs<TS>& a, cudaStream_
   const int tiles_x = (a.nx + TX - 1) / TX;
   const int ntiles = tiles_x * ((a.ny + TY - 1) / TY);
   int grid = per_sm[stage == 1 ? 0 : 1] * nsm;
+  if (a.max_ctas > 0 && grid > a.max_ctas) grid = a.max_ctas;
   if (grid > ntiles) grid = ntiles;
   const long long spin = 1LL << 26;
   if (stage == 1) k1<<<grid, T::NT, smem, st>>>(a, mc0, msl, tiles_x, ntiles, spin);

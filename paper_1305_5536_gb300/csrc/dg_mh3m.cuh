@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) mh3m_kernel(const Stage3DArgs<TS
     sp = (fabs(W[1]) + fast_speed(G, W[0], W[4], b2, W[5])) / dx +
          (fabs(W[2]) + fast_speed(G, W[0], W[4], b2, W[6])) / dy +
          (fabs(W[3]) + fast_speed(G, W[0], W[4], b2, W[7])) / dz;
-    if (!(sp >= TC(0))) { err |= ERR_NONPHYS; sp = TC(0); }
+    if (!courant_ok(sp, W[0], W[4])) { err |= ERR_NONPHYS; sp = TC(0); }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

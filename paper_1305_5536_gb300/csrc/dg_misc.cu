@@ -148,7 +148,12 @@ __global__ void cfl_kernel(int eq, int dim, StateBuf<TS> s, int nx, int ny, int 
       mag = TC(0.5) * (bx * bx + by * by + bz * bz);
     }
     TC p = G.gm1 * ((TC)s.c0[ie * ncell + i] - kin - mag);
-    if (!(rho > TC(0) && p > TC(0))) { err |= ERR_NONPHYS; continue; }
+    // a non-finite density or pressure is as non-physical as a negative one (an
+    // infinite density would give a zero signal speed)
+    if (!(rho > TC(0) && p > TC(0) && rho < TC(INFINITY) && p < TC(INFINITY))) {
+      err |= ERR_NONPHYS;
+      continue;
+    }
     TC sp;
     if (eq == 1) {
       TC b2 = bx * bx + by * by + bz * bz;

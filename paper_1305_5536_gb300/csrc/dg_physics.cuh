@@ -48,11 +48,38 @@ __device__ __forceinline__ float rsqrtv(float x) { return sqrtf(x); }
 
 // Conversions between the FP64 cell averages and the arithmetic type.  For the
 // FP32 path they are done with integer operations on the IEEE-754 bit patterns,
-// because GB300 executes FP64<->FP32 conversions on its narrow FP64 pipe.
-//   to_tc(double): rebias the exponent (1023 -> 127), keep the top 23 mantissa
-//     bits rounded to nearest (ties away from zero); magnitudes below the
-//     smallest normal float become 0 (the state never holds such values).
-//   to_f64(float): exact widening; subnormal floats become 0.
+// because GB300 executes FP64<->FP32 conversions on its narrow FP64 pipe.  The
+// word-level rules are plain functions of the bit patterns (host and device), so
+// that they can be checked on the CPU:
+//   f32_bits_of_f64(hi, lo): rebias the exponent (1023 -> 127), keep the top 23
+//     mantissa bits rounded to nearest (ties away from zero).  Magnitudes below
+//     the smallest normal float become a zero of the same sign; magnitudes that
+//     round to 2^128 or above become an infinity of the same sign; infinities stay
+//     infinities and every NaN becomes the quiet NaN 0x7fc00000 (with its sign).
+//   f64_words_of_f32(u): exact widening; subnormal floats become a zero of the
+//     same sign, infinities and NaNs keep their class (a NaN keeps its payload).
+__host__ __device__ __forceinline__ unsigned f32_bits_of_f64(unsigned h0, unsigned l0) {
+  const unsigned mag = h0 & 0x7fffffffu;                   // magnitude before rounding
+  const unsigned lo = l0 + 0x10000000u;                     // round at the float's last bit
+  const unsigned hi = mag + (lo < l0 ? 1u : 0u);            // magnitude, with the carry
+  unsigned r = ((hi - (896u << 20)) << 3) | (lo >> 29);
+  r = hi < (897u << 20) ? 0u : r;                           // below the float range: zero
+  r = hi >= (1151u << 20) ? 0x7f800000u : r;                // rounds to 2^128 or above: inf
+  const bool special = mag >= 0x7ff00000u;                  // the double is inf or NaN
+  const bool nan = mag > 0x7ff00000u || (mag == 0x7ff00000u && l0 != 0u);
+  r = special ? (nan ? 0x7fc00000u : 0x7f800000u) : r;
+  return r | (h0 & 0x80000000u);
+}
+__host__ __device__ __forceinline__ void f64_words_of_f32(unsigned u, unsigned& hi,
+                                                          unsigned& lo) {
+  const unsigned m = u & 0x7fffffffu;
+  const unsigned e = m >= 0x7f800000u ? (0x7ff00000u | ((m & 0x007fffffu) >> 3))  // inf / NaN
+                                      : ((m >> 3) + (896u << 20));
+  const bool tiny = m < 0x00800000u;
+  hi = (u & 0x80000000u) | (tiny ? 0u : e);
+  lo = tiny ? 0u : m << 29;
+}
+
 template <class T> struct Cvt;
 template <> struct Cvt<double> {
   __device__ __forceinline__ static double to_tc(double x) { return x; }
@@ -62,21 +89,24 @@ template <> struct Cvt<float> {
   // On the two 32-bit halves: masking the sign of the 64-bit pattern would be
   // compiled as a double absolute value, an FP64-pipe instruction.
   __device__ __forceinline__ static float to_tc(double x) {
-    const unsigned h0 = (unsigned)__double2hiint(x), l0 = (unsigned)__double2loint(x);
-    const unsigned lo = l0 + 0x10000000u;                       // round at the float's last bit
-    const unsigned hi = (h0 & 0x7fffffffu) + (lo < l0 ? 1u : 0u);  // magnitude, with the carry
-    unsigned r = ((hi - (896u << 20)) << 3) | (lo >> 29);
-    r = hi < (897u << 20) ? 0u : r;
-    return __int_as_float((int)(r | (h0 & 0x80000000u)));
+    return __int_as_float((int)f32_bits_of_f64((unsigned)__double2hiint(x),
+                                               (unsigned)__double2loint(x)));
   }
   __device__ __forceinline__ static double to_f64(float f) {
-    const unsigned u = (unsigned)__float_as_int(f);
-    const unsigned m = u & 0x7fffffffu;
-    const unsigned hi = (u & 0x80000000u) | ((m >> 3) + (896u << 20));
-    const unsigned lo = m << 29;
-    return m < 0x00800000u ? 0.0 : __hiloint2double((int)hi, (int)lo);
+    unsigned hi, lo;
+    f64_words_of_f32((unsigned)__float_as_int(f), hi, lo);
+    return __hiloint2double((int)hi, (int)lo);
   }
 };
+
+// A Courant signal speed sp of a cell with density rho and pressure p that a time
+// step can be taken from: finite and non-negative, and the state itself finite
+// (an infinite density has zero velocity and sound speed, so sp alone would pass).
+template <class T>
+__device__ __forceinline__ bool courant_ok(T sp, T rho, T p) {
+  const T inf = T(INFINITY);
+  return sp >= T(0) && sp < inf && rho < inf && p < inf;
+}
 
 // x / 2 without the FP64 pipe: the exponent field lowered by one (integer work on
 // the high word).  Exact for finite |x| >= 2^-1021; infinities and NaNs are

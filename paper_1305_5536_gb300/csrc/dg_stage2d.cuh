@@ -375,7 +375,7 @@ __device__ __forceinline__ void courant_commit2d(const Stage2DArgs<TS>& A, const
       cy = fast_speed(G, W[0], W[3], b2, W[5]);
     }
     sp = (fabs(W[1]) + cx) / dx + (fabs(W[2]) + cy) / dy;
-    if (!(sp >= TC(0))) { err |= ERR_NONPHYS; sp = TC(0); }
+    if (!courant_ok(sp, W[0], W[3])) { err |= ERR_NONPHYS; sp = TC(0); }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

@@ -67,20 +67,33 @@ __global__ void __launch_bounds__(TX * TY)
   }
   __syncthreads();
   unsigned phase = 0;
+  // `pending`: a TMA load of this CTA's current tile is in flight (the same value
+  // in every thread).  After a wait has run out the CTA stops using TMA: it records
+  // ERR_TIMEOUT (the launch's results are then invalid), waits once more, bounded,
+  // for the copy in flight, and stages the rest of its tiles element by element.
+  bool tma_ok = true;
   int t = blockIdx.x;
-  if (tid == 0 && t < ntiles) {
-    const int ty = t / tiles_x, tx = t - ty * tiles_x;
-    if (interior(tx * TX, ty * TY)) issue(tx * TX, ty * TY);
-  }
+  bool pending = t < ntiles && interior((t % tiles_x) * TX, (t / tiles_x) * TY);
+  if (tid == 0 && pending) issue((t % tiles_x) * TX, (t / tiles_x) * TY);
   for (; t < ntiles; t += gridDim.x) {
     const int ty = t / tiles_x, tx = t - ty * tiles_x;
     const int i0 = tx * TX, j0 = ty * TY;
     __syncthreads();  // the previous tile is done with shared memory
     stage2d_setup<EQ, TC, TS, TX, TY>(A, i0, j0, M, S);
     __syncthreads();
-    if (interior(i0, j0)) {
-      if (!mbar_wait_bounded(&bar, phase, spin_limit)) atomicOr(&S.err, ERR_TIMEOUT);
+    bool use_raw = false;
+    if (pending) {
+      const bool late = !mbar_wait_bounded(&bar, phase, spin_limit);
+      if (__syncthreads_or(late)) {
+        if (tid == 0) atomicOr(&S.err, ERR_TIMEOUT);
+        (void)mbar_wait_bounded(&bar, phase, spin_limit);  // drain the copy in flight
+        tma_ok = false;
+      } else {
+        use_raw = true;
+      }
       phase ^= 1u;
+    }
+    if (use_raw) {
       for (int e = tid; e < T::NV * T::R2; e += T::NT) M.c0[e] = Cvt<TC>::to_tc(raw_c0[e]);
       for (int e = tid; e < T::NS * T::R1; e += T::NT) {
         const int v = e / T::R1, r = e - v * T::R1;
@@ -94,10 +107,8 @@ __global__ void __launch_bounds__(TX * TY)
     __syncthreads();
     // the raw boxes are free: start loading the next tile of this CTA
     const int tn = t + gridDim.x;
-    if (tid == 0 && tn < ntiles) {
-      const int tyn = tn / tiles_x, txn = tn - tyn * tiles_x;
-      if (interior(txn * TX, tyn * TY)) issue(txn * TX, tyn * TY);
-    }
+    pending = tma_ok && tn < ntiles && interior((tn % tiles_x) * TX, (tn / tiles_x) * TY);
+    if (tid == 0 && pending) issue((tn % tiles_x) * TX, (tn / tiles_x) * TY);
     stage2d_compute<EQ, TC, TS, TX, TY, STAGE>(A, i0, j0, (unsigned)ntiles, M, S);
   }
 }

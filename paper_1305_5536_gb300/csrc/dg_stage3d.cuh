@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
       prims3d<TC>(G, c, W, err);
       TC cs = sqrt(G.g * W[4] / W[0]);
       sp = (fabs(W[1]) + cs) / dx + (fabs(W[2]) + cs) / dy + (fabs(W[3]) + cs) / dz;
-      if (!(sp >= TC(0))) { err |= ERR_NONPHYS; sp = TC(0); }
+      if (!courant_ok(sp, W[0], W[4])) { err |= ERR_NONPHYS; sp = TC(0); }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

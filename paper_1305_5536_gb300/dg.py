@@ -29,7 +29,8 @@ _STATUS = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_ENO
 SYMBOLS = ["dg_num_planes", "dg_init", "dg_init_batch", "dg_destroy", "dg_last_error",
            "dg_set_state", "dg_get_state", "dg_step", "dg_sync", "dg_get_times", "dg_totals",
            "dg_divb", "dg_adjoint_step", "dg_record", "dg_adjoint", "dg_profile",
-           "dg_profile_read", "dg_stage_bytes", "dg_totals_noalloc", "dg_kernel_name"]
+           "dg_profile_read", "dg_stage_bytes", "dg_totals_noalloc", "dg_kernel_name",
+           "dg_record_generation"]
 
 
 class DGError(RuntimeError):
@@ -88,6 +89,8 @@ def load():
     L.dg_stage_bytes.argtypes = [vp, c_int]
     L.dg_stage_bytes.restype = c_double
     L.dg_totals_noalloc.argtypes = [pcfg, vp, vp, c_int, vp]
+    L.dg_record_generation.argtypes = [vp]
+    L.dg_record_generation.restype = ctypes.c_longlong
     L.dg_kernel_name.argtypes = [vp]
     L.dg_kernel_name.restype = ctypes.c_char_p
     _lib = L
@@ -253,6 +256,10 @@ class DGSolver:
         self._check(self._L.dg_record(self._h, int(nsteps), float(dt), ctypes.byref(t)))
         return t.value
 
+    def record_generation(self):
+        """Changes whenever the recorded trajectory does (see dg_record_generation)."""
+        return self._L.dg_record_generation(self._h)
+
     def adjoint(self, lam_N, lam_0=None):
         import torch
         if lam_0 is None:
@@ -311,10 +318,19 @@ def _rollout_fn():
                 solver.set_state(u0.detach().contiguous())
                 solver.record(nsteps, dt)
                 ctx.solver = solver
+                ctx.generation = solver.record_generation()
                 return solver.get_state(device=u0.device)
 
             @staticmethod
             def backward(ctx, g):
+                # the solver keeps one recording: another rollout, a set_state or a
+                # step since this forward pass has replaced or ended it
+                if ctx.solver.record_generation() != ctx.generation:
+                    raise RuntimeError(
+                        "the solver's recorded trajectory changed after this rollout's "
+                        "forward pass (another rollout, set_state or step on the same "
+                        "solver); run backward before reusing the solver, or give each "
+                        "rollout its own solver")
                 return ctx.solver.adjoint(g.contiguous()), None, None, None
 
         _ROLLOUT = DGRollout

@@ -91,3 +91,28 @@ def class_rel_err(got, ref, eq, dim):
         if e > worst:
             worst, where = e, g
     return worst, where
+
+
+def class_errors(got, ref, eq, dim):
+    """[(variable, class, error / the class's own largest |ref|, largest |ref|)] for
+    every (variable, coefficient class): the per-class figure that the polynomial
+    error above replaces (reported, not a bar)."""
+    nT = 4 if dim == 2 else 5
+    names = (["rho", "mx", "my", "E"] if dim == 2 else ["rho", "mx", "my", "mz", "E"])
+    out = []
+    for v in range(nT):
+        for cls, planes in (("average", [v * (dim + 1)]),
+                            ("derivatives", list(range(v * (dim + 1) + 1, (v + 1) * (dim + 1))))):
+            s = np.abs(ref[planes]).max()
+            d = np.abs(got[planes] - ref[planes]).max()
+            out.append((names[v], cls, d / s if s > 0 else d, s))
+    if eq == 1:
+        b0 = nT * (dim + 1)
+        nb = dim
+        nd = 3 if dim == 2 else 8
+        for cls, planes in (("average", list(range(b0, b0 + nb))),
+                            ("derivatives", list(range(b0 + nb, b0 + nb + nd)))):
+            s = np.abs(ref[planes]).max()
+            d = np.abs(got[planes] - ref[planes]).max()
+            out.append(("B", cls, d / s if s > 0 else d, s))
+    return out

@@ -165,3 +165,55 @@ def test_autograd_rollout_fp32_gradient():
     f = lambda u: float((_forward_fixed(n, u, dts, "fp64", 0)[0] ** 2).sum())
     fd = (f(u0 + eps * d) - f(u0 - eps * d)) / (2 * eps)
     assert abs(float((g * d).sum()) - fd) < 2e-4 * abs(fd)
+
+
+def test_step_between_recordings_ends_the_first_one():
+    """dg_step between two dg_record calls ends the first recording: dg_adjoint has
+    nothing to run back over until the next dg_record, which starts a new recording
+    from the state the steps reached -- its gradient is that of a fresh recording
+    from that state."""
+    import torch
+    n = (24, 24)
+    u0, _ = ics.euler2d_random_density(n, kmax=4)
+    lam = torch.from_numpy(np.random.default_rng(12).standard_normal(u0.shape)).cuda()
+    s = dg.DGSolver("euler", 2, n, precision="fp64", limiter=0, ckpt_every=2)
+    s.set_state(u0)
+    g0 = s.record_generation()
+    s.record(3)
+    g1 = s.record_generation()
+    assert g1 != g0
+    s.step(2, sync=True)
+    assert s.record_generation() != g1
+    with pytest.raises(dg.DGError) as ei:
+        s.adjoint(lam)
+    assert ei.value.status == dg.DG_ESTATE
+    u_mid = s.get_state()
+    s.record(4)
+    got = s.adjoint(lam).cpu().numpy()
+    s.close()
+    fresh = dg.DGSolver("euler", 2, n, precision="fp64", limiter=0, ckpt_every=2)
+    fresh.set_state(u_mid)
+    fresh.record(4)
+    ref = fresh.adjoint(lam).cpu().numpy()
+    fresh.close()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_second_rollout_on_one_solver_refuses_the_first_backward():
+    """A solver keeps one recording: after a second rollout on it, the first
+    rollout's backward pass raises instead of returning the second trajectory's
+    gradient; the second backward works."""
+    import torch
+    n = (16, 16)
+    ua, _ = ics.euler2d_random_density(n, kmax=4)
+    ub, _ = ics.euler2d_random_density(n, kmax=4, seed=77)
+    s = dg.DGSolver("euler", 2, n, precision="fp64", limiter=0, ckpt_every=3)
+    xa = torch.from_numpy(ua).cuda().requires_grad_(True)
+    xb = torch.from_numpy(ub).cuda().requires_grad_(True)
+    ya = dg.rollout(xa, s, 4)
+    yb = dg.rollout(xb, s, 4)
+    with pytest.raises(RuntimeError, match="recorded trajectory changed"):
+        (ya[0] ** 2).sum().backward()
+    (yb[0] ** 2).sum().backward()
+    assert xb.grad is not None and torch.isfinite(xb.grad).all()
+    s.close()

@@ -12,7 +12,7 @@ import pytest
 import oracle as O
 from paper_1305_5536_gb300 import dg, ics
 
-from helpers import class_rel_err, poly_rel_err
+from helpers import class_errors, class_rel_err, poly_rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -80,8 +80,11 @@ def test_euler2d_smooth_wave_workload_fp64_50_steps():
     assert err < 1e-11, (err, where)
 
 
-def test_orszag_tang_512_one_step_full_size():
-    """Full-size Orszag-Tang 512x512 (FP64 and FP32), one step, every cell."""
+def test_orszag_tang_512_one_step_full_size(capsys):
+    """Full-size Orszag-Tang 512x512 (FP64 and FP32), one step, every cell; the
+    conservation totals and the Stokes div B of the GPU's new state against the
+    oracle's on that state.  Also reported (printed, not a bar): the error of every
+    (variable, coefficient class) relative to that class's own largest value."""
     n = (512, 512)
     u0 = ics.orszag_tang(n)
     P = O.Problem(O.MHD, 2, n)
@@ -94,9 +97,20 @@ def test_orszag_tang_512_one_step_full_size():
         tnext = s.times()[1][0]
         assert abs(tnext - dt) < (1e-14 if prec == "fp64" else 1e-6) * dt
         s.step(1, dt=dt, sync=True)
-        err, where = poly_rel_err(s.get_state(), ref, 1, 2, P.h)
+        got = s.get_state()
+        err, where = poly_rel_err(got, ref, 1, 2, P.h)
+        tot = s.totals()[0]
+        divb = s.divb()
         s.close()
         assert err < TOL[prec], (prec, err, where)
+        otot = P.totals(got)
+        np.testing.assert_allclose(tot, otot, rtol=1e-14, atol=1e-15 * np.abs(otot).max())
+        np.testing.assert_allclose(divb, P.divb(got), rtol=0, atol=1e-11 * np.abs(got[12:14]).max()
+                                   / P.h[0])
+        with capsys.disabled():
+            print("\nOT 512^2 %s one step: poly_rel_err %.3e (%s)" % (prec, err, where))
+            for name, g, e, scale in class_errors(got, ref, 1, 2):
+                print("  %-4s %-12s max|ref| %.3e  err/own max %.3e" % (name, g, scale, e))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -112,6 +126,56 @@ def test_conservation_and_divb_on_gpu(prec):
     assert np.abs(t1 - t0).max() < (1e-13 if prec == "fp64" else 1e-6) * scale
     P = O.Problem(O.MHD, 2, n)
     np.testing.assert_allclose(s.divb(), P.divb(s.get_state()), atol=1e-12)
+
+
+@pytest.mark.parametrize("eq,dim,n", [("euler", 2, (37, 29)), ("mhd", 2, (40, 24)),
+                                      ("euler", 3, (12, 10, 6)), ("mhd", 3, (10, 8, 6))])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_totals_match_oracle(eq, dim, n, prec):
+    """dg_totals (Neumaier-compensated FP64 sums on the GPU, times the cell volume)
+    against the oracle's totals of the same state, after a few steps, on
+    anisotropic cells: every conserved variable including the field averages."""
+    box = (1.0, 0.7, 1.3)[:dim]
+    if dim == 2:
+        u0 = _generic_euler(n) if eq == "euler" else ics.orszag_tang(n)
+    else:
+        u0 = ics.kh3d(n) if eq == "euler" else ics.orszag_tang_3d(n)
+    s = dg.DGSolver(eq, dim, n, box=box + (1.0,) * (3 - dim), precision=prec)
+    s.set_state(u0)
+    s.step(3, sync=True)
+    tot = s.totals()[0]
+    P = O.Problem(O.MHD if eq == "mhd" else O.EULER, dim, n, box=box)
+    ref = P.totals(s.get_state())
+    s.close()
+    assert tot.size == ref.size == dg.num_totals(eq, dim)
+    np.testing.assert_allclose(tot, ref, rtol=1e-14, atol=1e-15 * np.abs(ref).max())
+
+
+def test_nonfinite_averages_are_reported_not_converted_fp32():
+    """FP32 path: a NaN density average and an infinite energy average are
+    non-physical states (DG_ENONPHYS from set_state, and from the next step), and
+    the state read back keeps them non-finite instead of turning them into finite
+    numbers."""
+    n = (16, 12)
+    u0 = _generic_euler(n)
+    for plane, val in ((0, np.nan), (9, np.inf), (0, 1e300)):
+        u = u0.copy()
+        u[plane, 5, 7] = val
+        s = dg.DGSolver("euler", 2, n, precision="fp32")
+        with pytest.raises(dg.DGError) as ei:
+            s.set_state(u)
+        assert ei.value.status == dg.DG_ENONPHYS
+        back = s.get_state()
+        if np.isfinite(val):
+            assert back[plane, 5, 7] == val
+        else:
+            assert not np.isfinite(back[plane, 5, 7])
+        with pytest.raises(dg.DGError) as ei:
+            s.step(1, dt=1e-4, sync=True)
+        assert ei.value.status == dg.DG_ENONPHYS
+        if np.isnan(val):  # a NaN average stays NaN through the step's update
+            assert np.isnan(s.get_state()[plane, 5, 7])
+        s.close()
 
 
 def test_free_stream_gpu():

@@ -46,3 +46,34 @@ def test_every_tile_variant_one_and_two_steps(variant, prec, eq, n, monkeypatch)
     err, where = poly_rel_err(s.get_state(), ref2, 1 if eq == "mhd" else 0, 2, P.h)
     assert err < 3 * TOL[prec], (err, where)
     s.close()
+
+
+@pytest.mark.parametrize("variant", [3, 4])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("eq", ["euler", "mhd"])
+def test_tma_kernel_many_tiles_per_cta(variant, prec, eq, monkeypatch):
+    """The persistent TMA kernels with their grid capped at 3 CTAs (test hook
+    DG_TEST_MAX_CTAS): each CTA walks 20-40 tiles, so the next-tile prefetch into
+    the raw boxes, the reuse of shared memory across tiles and the seam tiles'
+    element-wise staging between TMA tiles all run; the result must still be the
+    oracle's."""
+    monkeypatch.setenv("DG_TILE_VARIANT", str(variant))
+    monkeypatch.setenv("DG_TEST_MAX_CTAS", "3")
+    n = (128, 96)
+    u0 = _state(eq, n)
+    P = O.Problem(O.MHD if eq == "mhd" else O.EULER, 2, n)
+    dt = 0.5 * P.cfl_dt(u0)[0]
+    ref, fl = P.step(u0, dt)
+    assert fl == 0
+    ref2, fl = P.step(ref, dt)
+    assert fl == 0
+    s = dg.DGSolver(eq, 2, n, precision=prec)
+    s.set_state(u0)
+    assert "stage2d_tma_kernel" in s.kernel_name()
+    s.step(1, dt=dt, sync=True)
+    err, where = poly_rel_err(s.get_state(), ref, 1 if eq == "mhd" else 0, 2, P.h)
+    assert err < TOL[prec], (err, where)
+    s.step(1, dt=dt, sync=True)
+    err, where = poly_rel_err(s.get_state(), ref2, 1 if eq == "mhd" else 0, 2, P.h)
+    assert err < 3 * TOL[prec], (err, where)
+    s.close()
