@@ -211,10 +211,29 @@ dg_status dg_adjoint(dg_ctx* ctx, const double* lam_N, double* lam_0);
 dg_status dg_totals_noalloc(const dg_config* cfg, const double* u, double* out,
                             int out_on_device, void* cuda_stream);
 
+/* Measured fused multiply-add throughput of the current device (a diagnostic for
+ * roofline fractions; the paper has no counterpart): every SM runs independent
+ * FMA chains in FP64 (precision DG_FP64) or FP32 (DG_FP32) for ~20 ms, timed
+ * with CUDA events on a private stream; *flops_per_s = 2 x FMAs per second, the
+ * best of several runs.  The FP64 stage kernels are bound by the FP64 pipe, and
+ * this is the peak their FP64 flop rate is reported against.  Allocates a small
+ * buffer; synchronises.  Failures are described by dg_last_error(NULL). */
+dg_status dg_peak_fma(int precision, double* flops_per_s);
+
 /* Kernel timing with CUDA events recorded on the context stream around every
  * stage-kernel launch (enable != 0), or stop (0).  Enabling clears the record
  * and disables CUDA-graph replay for the recorded steps. */
 dg_status dg_profile(dg_ctx* ctx, int enable);
+
+/* Per-phase SM cycles of the stage kernels (2D and 3D SSP-RK2 stage kernels with
+ * per-element staging) summed over their CTAs since profiling was last enabled.
+ * Only the library's profiling build (compiled with DG_PHASE_PROFILE) counts
+ * them; the normal build returns DG_EINVAL.  cycles[s * 16 + k] for stage s = 0, 1
+ * and phase k; n >= 32.  2D phases: 0 staging, 1 primitives, 2 limiter, 3 faces,
+ * 4 per-cell right-hand side and combination, 5 Courant reduction; 3D phases:
+ * 0 staging and primitives, 1 limiter, 2 volume integral, 3/5/7 x/y/z faces,
+ * 4/6/8 their gathers, 9 combination, 10 Courant reduction.  Synchronises. */
+dg_status dg_phase_cycles(dg_ctx* ctx, double* cycles, int n);
 
 /* Totals of the recorded kernel times: ms[k] and launches[k] for k = 0 (stage 1)
  * and 1 (stage 2 incl. the fused time-step reduction).  A batch of 2D problems

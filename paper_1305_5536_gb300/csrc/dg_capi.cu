@@ -80,6 +80,9 @@ struct dg_ctx {
   // test hook DG_TEST_MAX_CTAS: cap on the grids of the persistent (TMA, batched)
   // kernels, so that every CTA processes many tiles
   int max_ctas = 0;
+  // phase cycle counters of the stage kernels (profiling build; 2 stages x
+  // kPhaseSlots), allocated and cleared when profiling is enabled
+  unsigned long long* phase_dev = nullptr;
   std::string kname;
 };
 
@@ -252,6 +255,7 @@ cudaError_t launch_stage_t(dg_ctx* c, int stage, int in, int base, int out, doub
       a.lim_sl = lim >= 0 ? sbuf<TS>(c, lim, p).sl : nullptr;
       a.ctl = c->ctl + ip;
       a.max_ctas = c->max_ctas;
+      a.phase = c->prof ? c->phase_dev : nullptr;
       cudaError_t e = launch_stage2d(c->eq, c->variant < 0 ? 0 : c->variant, stage, a,
                                      c->launch_stream);
       if (e != cudaSuccess) return e;
@@ -266,6 +270,7 @@ cudaError_t launch_stage_t(dg_ctx* c, int stage, int in, int base, int out, doub
       a.out = sbuf<TS>(c, out, p);
       a.lim_sl = lim >= 0 ? sbuf<TS>(c, lim, p).sl : nullptr;
       a.ctl = c->ctl + ip;
+      a.phase = c->prof ? c->phase_dev : nullptr;
       const int v = c->variant < 0 ? 0 : c->variant;
       cudaError_t e = c->eq == DG_MHD ? launch_stage3m(v, stage, a, c->launch_stream)
                                       : launch_stage3d(v, stage, a, c->launch_stream);
@@ -767,6 +772,7 @@ void dg_destroy(dg_ctx* c) {
   cudaFree(c->totals_dev);
   for (int v = 0; v < 3; ++v) cudaFree(c->btab[v]);
   cudaFree(c->bar);
+  cudaFree(c->phase_dev);
   if (c->ctl_host) cudaFreeHost(c->ctl_host);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
@@ -884,9 +890,29 @@ dg_status dg_profile(dg_ctx* c, int enable) {
       cudaEventDestroy(e.b);
     }
     c->evs.clear();
+#ifdef DG_PHASE_PROFILE
+    const size_t bytes = 2 * kPhaseSlots * sizeof(unsigned long long);
+    if (!c->phase_dev) CK(c, cudaMalloc(&c->phase_dev, bytes));
+    CK(c, cudaMemset(c->phase_dev, 0, bytes));
+#endif
   }
   c->prof = enable != 0;
   return DG_OK;
+}
+
+dg_status dg_phase_cycles(dg_ctx* c, double* cycles, int n) {
+  if (!c || !cycles) return fail(c, DG_EINVAL, "null argument");
+  if (n < 2 * kPhaseSlots) return fail(c, DG_EINVAL, "need room for %d counters", 2 * kPhaseSlots);
+#ifdef DG_PHASE_PROFILE
+  if (!c->phase_dev) return fail(c, DG_ESTATE, "enable profiling (dg_profile) first");
+  unsigned long long h[2 * kPhaseSlots];
+  CK(c, cudaStreamSynchronize(c->stream));
+  CK(c, cudaMemcpy(h, c->phase_dev, sizeof(h), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < 2 * kPhaseSlots; ++k) cycles[k] = (double)h[k];
+  return DG_OK;
+#else
+  return fail(c, DG_EINVAL, "this library was built without phase profiling (DG_PHASE_PROFILE)");
+#endif
 }
 
 dg_status dg_profile_read(dg_ctx* c, double ms[2], long long launches[2]) {

@@ -47,6 +47,35 @@ template <class T> __device__ __forceinline__ const Gas<T>& gas_of(const GasPair
 template <> __device__ __forceinline__ const Gas<double>& gas_of<double>(const GasPair& g) { return g.d; }
 template <> __device__ __forceinline__ const Gas<float>& gas_of<float>(const GasPair& g) { return g.f; }
 
+// Phase profiling of the stage kernels, compiled in only by the profiling build
+// (-DDG_PHASE_PROFILE; the normal build has no stamps).  Thread 0 of every CTA
+// stamps clock64() at the end of each phase -- after the barrier that closes it,
+// or after its own work where no barrier follows -- and adds the SM cycles since
+// its previous stamp to that phase's counter: acc[(stage - 1) * kPhaseSlots +
+// phase].  Summed over the CTAs, the counters give each phase's share of the
+// kernel's time.
+constexpr int kPhaseSlots = 16;
+struct PhaseStamp {
+#ifdef DG_PHASE_PROFILE
+  long long t;
+  unsigned long long* acc;
+  __device__ __forceinline__ void begin(unsigned long long* a, int stage) {
+    acc = a ? a + (stage - 1) * kPhaseSlots : nullptr;
+    t = clock64();
+  }
+  __device__ __forceinline__ void mark(int phase) {
+    if (acc && threadIdx.x == 0) {
+      const long long now = clock64();
+      atomicAdd(acc + phase, (unsigned long long)(now - t));
+      t = now;
+    }
+  }
+#else
+  __device__ __forceinline__ void begin(unsigned long long*, int) {}
+  __device__ __forceinline__ void mark(int) {}
+#endif
+};
+
 // Arguments of one stage launch on one periodic 2D grid.
 template <class TS>
 struct Stage2DArgs {
@@ -67,6 +96,7 @@ struct Stage2DArgs {
   // Largest grid of a persistent launch (the TMA kernels), 0 = as many CTAs as are
   // resident.  Set only by a test hook, so that each CTA walks many tiles.
   int max_ctas = 0;
+  unsigned long long* phase = nullptr;  // phase cycle counters (profiling build)
 };
 
 // Arguments of one stage launch on one periodic 3D grid.
@@ -83,7 +113,33 @@ struct Stage3DArgs {
   StateBuf<TS> out;
   TS* lim_sl;  // as for Stage2DArgs
   Ctl* ctl;
+  unsigned long long* phase = nullptr;  // phase cycle counters (profiling build)
 };
+
+// The cells of a TX x TY x TZ tile and its six face slabs (the halo-1 box
+// without its edges and corners): the cells whose limited slopes the face fluxes
+// read.  Cell e (0 <= e < ring3d_count) as halo-1 box coordinates (rx, ry, rz):
+// first the tile, then the x, y and z slabs (low side, then high side).
+template <int TX, int TY, int TZ>
+__host__ __device__ constexpr int ring3d_count() {
+  return TX * TY * TZ + 2 * (TY * TZ + TX * TZ + TX * TY);
+}
+template <int TX, int TY, int TZ>
+__device__ __forceinline__ void ring3d_cell(int e, int& rx, int& ry, int& rz) {
+  constexpr int NT = TX * TY * TZ, SX = TY * TZ, SY = TX * TZ, SZ = TX * TY;
+  if (e < NT) {
+    rx = e % TX + 1; ry = (e / TX) % TY + 1; rz = e / (TX * TY) + 1;
+  } else if (e < NT + 2 * SX) {
+    const int k = e - NT, s = k >= SX, q = k - s * SX;
+    rx = s ? TX + 1 : 0; ry = q % TY + 1; rz = q / TY + 1;
+  } else if (e < NT + 2 * (SX + SY)) {
+    const int k = e - NT - 2 * SX, s = k >= SY, q = k - s * SY;
+    ry = s ? TY + 1 : 0; rx = q % TX + 1; rz = q / TX + 1;
+  } else {
+    const int k = e - NT - 2 * (SX + SY), s = k >= SZ, q = k - s * SZ;
+    rz = s ? TZ + 1 : 0; rx = q % TX + 1; ry = q / TX + 1;
+  }
+}
 
 __host__ __device__ __forceinline__ int wrap_index(int g, int n) {
   int r = g % n;

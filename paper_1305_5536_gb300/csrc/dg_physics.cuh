@@ -17,6 +17,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace dgk {
 
 enum : unsigned {
@@ -223,9 +225,18 @@ __device__ __forceinline__ T exact_pstar(const Gas<T>& G, T rL, T uL, T pL, T cL
   return p;
 }
 
+template <int NT>
+__device__ __forceinline__ void exact_flux_f32(const Gas<float>& G, float rL, float uL, float pL,
+                                               const float* vtL, float rR, float uR, float pR,
+                                               const float* vtR, float* F, unsigned& err);
+
 template <class T, int NT>
 __device__ __forceinline__ void exact_flux(const Gas<T>& G, T rL, T uL, T pL, const T* vtL, T rR,
                                            T uR, T pR, const T* vtR, T* F, unsigned& err) {
+  if constexpr (std::is_same<T, float>::value) {
+    exact_flux_f32<NT>(G, rL, uL, pL, vtL, rR, uR, pR, vtR, F, err);
+    return;
+  }
   if (!(rL > T(0) && pL > T(0) && rR > T(0) && pR > T(0))) {
     err |= ERR_NONPHYS;
     for (int q = 0; q < 3 + NT; ++q) F[q] = T(0);
@@ -286,6 +297,149 @@ __device__ __forceinline__ void exact_flux(const Gas<T>& G, T rL, T uL, T pL, co
   for (int a = 0; a < NT; ++a) kin += vt[a] * vt[a];
   const T E = pp * G.inv_gm1 + T(0.5) * rho * kin;
   const T mu = rho * u;
+  F[0] = mu;
+  F[1] = mu * u + pp;
+#pragma unroll
+  for (int a = 0; a < NT; ++a) F[2 + a] = mu * vt[a];
+  F[2 + NT] = u * (E + pp);
+}
+
+// ----------------------------------------------------------------------------
+// The exact Riemann solver of the FP32 path.  It computes the solution of
+// exact_flux (Toro's exact solver: Newton iteration for p* on f_L + f_R + du = 0
+// from the adaptive PVRS / TRRS / TSRS guess, sampled at x/t = 0) with the
+// arithmetic arranged for the FP32 pipes:
+//   * per side, the constants of the pressure function are formed once:
+//       shock       f = (p - pK) q,  q = (A_K / (p + B_K))^(1/2),
+//                   f' = q (1 - (p - pK) / (2 (p + B_K))) = q (1 - (p - pK) q^2 / (2 A_K)),
+//       rarefaction f = 2 cK / (g - 1) ((p/pK)^z - 1),  f' = (p/pK)^z cK / (g p),
+//     with A_K = 2 / ((g + 1) rho_K), B_K = (g - 1) / (g + 1) pK, z = (g - 1) / (2g);
+//     divisions become approximate reciprocals, square roots reciprocal square
+//     roots, powers exp2(e log2 x) (all within a few ulp);
+//   * both branches of f are evaluated and one is selected, so that lanes of a
+//     warp on different branches (near-equal states put p on either side of pK
+//     at random) do not serialise;
+//   * Newton converges quadratically: accepting the update p_n after a step of
+//     relative size delta leaves an error of about k delta^2 (k <= 1/2 for these
+//     pressure functions), so steps below 2e-4 are accepted (error < 2e-8, below
+//     the FP32 evaluation noise of f), and f_K(p*) for u* is taken from the last
+//     iteration's linearisation f_K(p) + f_K'(p)(p* - p) (error O(delta^2) again);
+//   * the sampling picks the side of the contact by select and mirrors the right
+//     side onto the left (u -> -u), so the unperturbed / shock-star /
+//     rarefaction-star choice is a select; only the transonic rarefaction fan,
+//     which is rare, is a branch.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float rcpf(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float sqrtf_pos(float x) { return x * rsqrtf(x); }  // x > 0
+
+template <int NT>
+__device__ __forceinline__ void exact_flux_f32(const Gas<float>& G, float rL, float uL, float pL,
+                                               const float* vtL, float rR, float uR, float pR,
+                                               const float* vtR, float* F, unsigned& err) {
+  if (!(rL > 0.0f && pL > 0.0f && rR > 0.0f && pR > 0.0f)) {
+    err |= ERR_NONPHYS;
+    for (int q = 0; q < 3 + NT; ++q) F[q] = 0.0f;
+    return;
+  }
+  constexpr float accept = 2e-4f;
+  const float ipL = rcpf(pL), ipR = rcpf(pR);
+  const float aL = G.g * pL * rcpf(rL), aR = G.g * pR * rcpf(rR);
+  const float cL = sqrtf_pos(aL), cR = sqrtf_pos(aR);
+  const float AiL = 0.5f * G.gp1 * rL, AiR = 0.5f * G.gp1 * rR;  // 1 / A_K
+  const float BL = G.g6 * pL, BR = G.g6 * pR;
+  const float CL = G.two_gm1 * cL, CR = G.two_gm1 * cR;          // 2 cK / (g - 1)
+  const float DL = cL * G.inv_g, DR = cR * G.inv_g;              // cK / g
+  const float du = uR - uL;
+  if (CL + CR <= du) err |= ERR_VACUUM;
+  // first guess (Toro's adaptive choice)
+  const float pmin = fminf(pL, pR), pmax = fmaxf(pL, pR);
+  float pv = 0.5f * (pL + pR) - 0.125f * du * (rL + rR) * (cL + cR);
+  pv = fmaxf(pv, 0.0f);
+  float p = pv;
+  if (!(pmax <= 2.0f * pmin && pmin <= pv && pv <= pmax)) {
+    if (pv < pmin) {  // two rarefactions
+      const float num = fmaxf(cL + cR - 0.5f * G.gm1 * du, 0.0f);
+      const float den = cL * exp2f(-G.z * __log2f(pL)) + cR * exp2f(-G.z * __log2f(pR));
+      p = exp2f(G.inv_z * __log2f(num * rcpf(den)));
+    } else {  // two shocks
+      const float gL = rsqrtf((BL + pv) * AiL), gR = rsqrtf((BR + pv) * AiR);
+      p = (gL * pL + gR * pR - du) * rcpf(gL + gR);
+    }
+  }
+  const float pfloor = 1e-10f * pmin;
+  if (!(p > pfloor)) p = pfloor;
+  // Newton iteration; fL, fR, dfL, dfR, p0 keep the last linearisation
+  float fL = 0.0f, fR = 0.0f, dfL = 1.0f, dfR = 1.0f, p0 = p;
+  bool conv = false;
+  for (int it = 0; it < Prec<float>::newton_max; ++it) {
+    const float rp = rcpf(p);
+    {
+      const float dp = p - pL;
+      const float q = rsqrtf((p + BL) * AiL);
+      const float fs = dp * q, dfs = q * (1.0f - 0.5f * dp * q * q * AiL);
+      const float qr = exp2f(G.z * __log2f(p * ipL));
+      const float fr = CL * (qr - 1.0f), dfr = qr * DL * rp;
+      const bool sh = p > pL;
+      fL = sh ? fs : fr;
+      dfL = sh ? dfs : dfr;
+    }
+    {
+      const float dp = p - pR;
+      const float q = rsqrtf((p + BR) * AiR);
+      const float fs = dp * q, dfs = q * (1.0f - 0.5f * dp * q * q * AiR);
+      const float qr = exp2f(G.z * __log2f(p * ipR));
+      const float fr = CR * (qr - 1.0f), dfr = qr * DR * rp;
+      const bool sh = p > pR;
+      fR = sh ? fs : fr;
+      dfR = sh ? dfs : dfr;
+    }
+    float pn = p - (fL + fR + du) * rcpf(dfL + dfR);
+    if (!(pn > pfloor)) pn = pfloor;
+    p0 = p;
+    const bool done = 2.0f * fabsf(pn - p) < accept * (pn + p);
+    p = pn;
+    if (done) { conv = true; break; }
+  }
+  if (!conv) err |= ERR_NEWTON;
+  // u* from the pressure functions at p*, by the last linearisation
+  const float dps = p - p0;
+  const float us = 0.5f * (uL + uR) + 0.5f * ((fR + dfR * dps) - (fL + dfL * dps));
+  // sample at x/t = 0 on the side of the contact that x/t = 0 lies on, the right
+  // side mirrored onto the left (velocities negated)
+  const bool left = us >= 0.0f;
+  const float sg = left ? 1.0f : -1.0f;
+  const float rK = left ? rL : rR, pK = left ? pL : pR, cK = left ? cL : cR;
+  const float ipK = left ? ipL : ipR;
+  const float w = sg * (left ? uL : uR), ws = sg * us;
+  const float pr = p * ipK;
+  const bool shock = p > pK;
+  const float Ssh = w - cK * sqrtf_pos(G.shk1 * pr + G.z);         // shock speed
+  const float rsh = rK * (pr + G.g6) * rcpf(G.g6 * pr + 1.0f);      // behind the shock
+  const float lpr = __log2f(pr);
+  const float cm = cK * exp2f(G.z * lpr);                           // sound speed behind the fan
+  const float rrf = rK * exp2f(G.inv_g * lpr);                      // isentropic star density
+  const bool unpert = shock ? Ssh >= 0.0f : w - cK >= 0.0f;
+  const bool fan = !shock && !unpert && !(ws - cm < 0.0f);
+  float rho = unpert ? rK : (shock ? rsh : rrf);
+  float u = unpert ? w : ws;
+  float pp = unpert ? pK : p;
+  if (fan) {
+    const float c = G.two_gp1 * (cK + 0.5f * G.gm1 * w);
+    const float lc = __log2f(c * rcpf(cK));
+    u = c;
+    rho = rK * exp2f(G.two_gm1 * lc);
+    pp = pK * exp2f(G.inv_z * lc);
+  }
+  u *= sg;
+  float vt[NT > 0 ? NT : 1];
+  float kin = u * u;
+#pragma unroll
+  for (int a = 0; a < NT; ++a) {
+    vt[a] = left ? vtL[a] : vtR[a];
+    kin += vt[a] * vt[a];
+  }
+  const float E = pp * G.inv_gm1 + 0.5f * rho * kin;
+  const float mu = rho * u;
   F[0] = mu;
   F[1] = mu * u + pp;
 #pragma unroll

@@ -415,10 +415,13 @@ __device__ __forceinline__ void courant_commit2d(const Stage2DArgs<TS>& A, const
 // the problem (the last of them to finish stage 2 publishes the Courant speed).
 // WENO = false compiles the WENO-type limiter out (for launches with limiter 0
 // or 1: its code raises the registers and stack of the common path).
+// `ph` (profiling build): phases 1 primitives, 2 limiter, 3 faces, 4 per-cell
+// right-hand side and combination, 5 Courant reduction and commit.
 template <int EQ, class TC, class TS, int TX, int TY, int STAGE, bool WENO = true>
 __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0, int j0,
                                                 unsigned nblk, const TileMem<TC>& M,
-                                                TileScalars<TX * TY>& S) {
+                                                TileScalars<TX * TY>& S,
+                                                PhaseStamp* ph = nullptr) {
   using Tr = Tr2<EQ>;
   constexpr int NV = Tr::NV, NS = Tr::NS, NP = Tr::NP, NF = Tr::NF;
   constexpr int R2X = TX + 4, R2Y = TY + 4, R2 = R2X * R2Y;
@@ -452,6 +455,7 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
     for (int q = 0; q < NP; ++q) s_w[q * R2 + r] = W[q];
   }
   __syncthreads();
+  if (ph) ph->mark(1);
 
   const TC dx = Cvt<TC>::to_tc(A.dx), dy = Cvt<TC>::to_tc(A.dy);
   TC hh[2] = {TC(0.5) * dx, TC(0.5) * dy};
@@ -479,6 +483,7 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
     }
   }
   __syncthreads();  // the primitives are dead from here: their space takes the fluxes
+  if (ph) ph->mark(2);
 
   // ---- faces: Riemann fluxes at the Gauss points, each face once
   const TC ox = dx * TC(0.28867513459481288225), oy = dy * TC(0.28867513459481288225);
@@ -520,6 +525,7 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
     }
   }
   __syncthreads();
+  if (ph) ph->mark(3);
 
   // ---- per cell: volume integral, face moments, mass matrix, RK combination
   const int lx = tid % TX, ly = tid / TX;
@@ -631,6 +637,7 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
     for (int k = 0; k < NS; ++k) A.out.sl[k * ncell + gc] = (TS)os[k];
   }
 
+  if (ph) ph->mark(4);
   if (STAGE == 2) {
     courant_commit2d<EQ, TC, TS, NT>(A, G, owner, o0, dx, dy, dt, nblk, err, S);
   } else {
@@ -638,6 +645,7 @@ __device__ __forceinline__ void stage2d_compute(const Stage2DArgs<TS>& A, int i0
     __syncthreads();
     if (tid == 0 && S.err) atomicOr(&A.ctl->err, S.err);
   }
+  if (ph) ph->mark(5);
 }
 
 
@@ -648,13 +656,16 @@ template <int EQ, class TC, class TS, int TX, int TY, int STAGE, bool WENO = tru
 __device__ __forceinline__ void stage2d_tile(const Stage2DArgs<TS>& A, int i0, int j0,
                                              unsigned nblk, unsigned char* smem_raw) {
   __shared__ TileScalars<TX * TY> S;
+  PhaseStamp ph;  // phase 0: set-up and staging (profiling build)
+  ph.begin(A.phase, STAGE);
   const TileMem<TC> M = tile_mem<EQ, TX, TY, TC>(smem_raw);
   stage2d_setup<EQ, TC, TS, TX, TY>(A, i0, j0, M, S);
   __syncthreads();
   if (STAGE == 2) stage2d_prefetch_base<EQ, TC, TS, TX, TY>(A, M);
   stage2d_load<EQ, TC, TS, TX, TY>(A, M);
   __syncthreads();
-  stage2d_compute<EQ, TC, TS, TX, TY, STAGE, WENO>(A, i0, j0, nblk, M, S);
+  ph.mark(0);
+  stage2d_compute<EQ, TC, TS, TX, TY, STAGE, WENO>(A, i0, j0, nblk, M, S, &ph);
 }
 
 // FP32: as many resident CTAs as 72 registers a thread allow for 128-thread

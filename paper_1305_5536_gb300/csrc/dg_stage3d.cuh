@@ -273,6 +273,11 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
   const size_t ncell = (size_t)A.ncell;
   const Gas<TC> G = gas_of<TC>(A.gas);
   unsigned err = 0;
+  // profiling build: phases 0 staging and primitives, 1 limiter, 2 volume
+  // integral, 3 + 2d faces and 4 + 2d their gather (d = 0, 1, 2), 9 combination
+  // and store, 10 Courant reduction and commit
+  PhaseStamp ph;
+  ph.begin(A.phase, STAGE);
   if (tid == 0) {
     s_err = 0;
     double dt = A.dt_override > 0.0 ? A.dt_override : A.cfl / A.ctl->vmax_cur;
@@ -306,18 +311,20 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
   }
   cp_async_wait_all();
   __syncthreads();
+  ph.mark(0);
 
   const TC dx = Cvt<TC>::to_tc(A.dx), dy = Cvt<TC>::to_tc(A.dy), dz = Cvt<TC>::to_tc(A.dz);
   const TC hh[3] = {TC(0.5) * dx, TC(0.5) * dy, TC(0.5) * dz};
   const TC oo[3] = {dx * TC(0.28867513459481288225), dy * TC(0.28867513459481288225),
                     dz * TC(0.28867513459481288225)};
 
-  // ---- limiter on the tile and its ring
+  // ---- limiter on the tile and its face slabs (the cells the faces read)
   if (A.limiter) {
-    for (int r1 = tid; r1 < R1; r1 += NT) {
-      int rz = r1 / (R1X * R1Y), rr = r1 - rz * (R1X * R1Y);
-      int ry = rr / R1X, rx = rr - ry * R1X;
-      int r2 = ((rz + 1) * R2Y + (ry + 1)) * R2X + (rx + 1);
+    for (int e = tid; e < ring3d_count<TX, TY, TZ>(); e += NT) {
+      int rx, ry, rz;
+      ring3d_cell<TX, TY, TZ>(e, rx, ry, rz);
+      const int r1 = (rz * R1Y + ry) * R1X + rx;
+      const int r2 = ((rz + 1) * R2Y + (ry + 1)) * R2X + (rx + 1);
       TC W[5], Wn[6][5], s[15];
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
@@ -338,6 +345,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
     }
     __syncthreads();
   }
+  ph.mark(1);
 
   // ---- per-cell state, volume integral
   const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
@@ -376,6 +384,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
       for (int d = 0; d < 3; ++d) rs[3 * v + d] = TC(1.5) / (hd[d] * hd[d]) * sF[d][v];
   }
 
+  ph.mark(2);
   // ---- faces, one orientation at a time (rolled loop: one copy of the solver)
   const TC hd[3] = {dx, dy, dz};
 #pragma unroll 1
@@ -412,6 +421,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
       for (int v = 0; v < 5; ++v) s_f[(v * FMAX + f) * 4 + g] = F[v];
     }
     __syncthreads();
+    ph.mark(3 + 2 * d);
     {
       const int fm = (lz * FY + ly) * FX + lx;
       const int fp = fm + (d == 0 ? 1 : (d == 1 ? FX : FX * FY));
@@ -420,6 +430,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
       else gather3d<2, TC>(s_f, FMAX, fm, fp, hd, rc0, rs);
     }
     __syncthreads();
+    ph.mark(4 + 2 * d);
   }
 
   // ---- Runge-Kutta combination
@@ -481,6 +492,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
 #pragma unroll
     for (int k = 0; k < 15; ++k) A.out.sl[k * ncell + gc] = (TS)os[k];
   }
+  ph.mark(9);
 
   if (STAGE == 2) {
     TC sp = TC(0);
@@ -530,6 +542,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
     __syncthreads();
     if (tid == 0 && s_err) atomicOr(&A.ctl->err, s_err);
   }
+  ph.mark(10);
 }
 
 }  // namespace dgk

@@ -394,12 +394,13 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3m_kernel(const Stage3DArgs
                     dz * TC(0.28867513459481288225)};
   const TC hd[3] = {dx, dy, dz};
 
-  // ---- limiter on the tile and its ring
+  // ---- limiter on the tile and its face slabs (the cells the faces read)
   if (A.limiter) {
-    for (int r1 = tid; r1 < R1; r1 += NT) {
-      int rz = r1 / (R1X * R1Y), rr = r1 - rz * (R1X * R1Y);
-      int ry = rr / R1X, rx = rr - ry * R1X;
-      int r2 = ((rz + 1) * R2Y + (ry + 1)) * R2X + (rx + 1);
+    for (int e = tid; e < ring3d_count<TX, TY, TZ>(); e += NT) {
+      int rx, ry, rz;
+      ring3d_cell<TX, TY, TZ>(e, rx, ry, rz);
+      const int r1 = (rz * R1Y + ry) * R1X + rx;
+      const int r2 = ((rz + 1) * R2Y + (ry + 1)) * R2X + (rx + 1);
       TC W[8], Wn[6][8], s[23];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {

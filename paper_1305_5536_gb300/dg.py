@@ -12,6 +12,9 @@ import numpy as np
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libdg.so")
+# The phase-profiling build of the same sources (phase_profile.py) is loaded
+# instead when DG_LIBRARY names it.
+LIB_PATH = os.environ.get("DG_LIBRARY") or LIB_PATH
 # Tile shapes chosen by the library's autotuner, per (equations, dimension,
 # precision, grid): the shipped cache makes runs reproducible; DG_TUNE_CACHE
 # names another file.
@@ -30,7 +33,7 @@ SYMBOLS = ["dg_num_planes", "dg_init", "dg_init_batch", "dg_destroy", "dg_last_e
            "dg_set_state", "dg_get_state", "dg_step", "dg_sync", "dg_get_times", "dg_totals",
            "dg_divb", "dg_adjoint_step", "dg_record", "dg_adjoint", "dg_profile",
            "dg_profile_read", "dg_stage_bytes", "dg_totals_noalloc", "dg_kernel_name",
-           "dg_record_generation"]
+           "dg_record_generation", "dg_peak_fma", "dg_phase_cycles"]
 
 
 class DGError(RuntimeError):
@@ -56,7 +59,7 @@ def load():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
+    if not os.path.exists(LIB_PATH) and not os.environ.get("DG_LIBRARY"):
         from . import _build
         _build.build()
     if not os.path.exists(LIB_PATH):
@@ -89,6 +92,8 @@ def load():
     L.dg_stage_bytes.argtypes = [vp, c_int]
     L.dg_stage_bytes.restype = c_double
     L.dg_totals_noalloc.argtypes = [pcfg, vp, vp, c_int, vp]
+    L.dg_peak_fma.argtypes = [c_int, P(c_double)]
+    L.dg_phase_cycles.argtypes = [vp, P(c_double), c_int]
     L.dg_record_generation.argtypes = [vp]
     L.dg_record_generation.restype = ctypes.c_longlong
     L.dg_kernel_name.argtypes = [vp]
@@ -277,11 +282,28 @@ class DGSolver:
         self._check(self._L.dg_profile_read(self._h, ms, n))
         return [ms[0], ms[1]], [n[0], n[1]]
 
+    def phase_cycles(self):
+        """Per-phase SM cycles of the stage kernels, shape (2 stages, 16 phases)
+        (profiling build only; dg_phase_cycles)."""
+        out = (ctypes.c_double * 32)()
+        self._check(self._L.dg_phase_cycles(self._h, out, 32))
+        return np.array(out[:]).reshape(2, 16)
+
     def kernel_name(self):
         return self._L.dg_kernel_name(self._h).decode()
 
     def stage_bytes(self, stage):
         return self._L.dg_stage_bytes(self._h, int(stage))
+
+
+def peak_fma(precision="fp64"):
+    """Measured FMA throughput of the current device in flop/s (dg_peak_fma)."""
+    L = load()
+    out = ctypes.c_double(0.0)
+    s = L.dg_peak_fma(DG_FP32 if precision in ("fp32", DG_FP32) else DG_FP64, ctypes.byref(out))
+    if s != DG_OK:
+        raise DGError(s, L.dg_last_error(None).decode())
+    return out.value
 
 
 def totals_noalloc(u, eq="euler", dim=2, n=(64, 64), box=(1.0, 1.0, 1.0), stream=None):
