@@ -678,9 +678,17 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the KH 256^3, FP64-peak and FP32-accuracy objects of the "
                          "default workload's line")
+    ap.add_argument("--only-adjoint", choices=["fp32", "fp64"],
+                    help="time only the adjoint workload in this precision (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.only_adjoint:
+        import torch
+        from paper_1305_5536_gb300 import dg, ics
+        print(json.dumps(measure_adjoint(dg, ics, torch, torch.cuda.current_stream(),
+                                         args.only_adjoint)))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

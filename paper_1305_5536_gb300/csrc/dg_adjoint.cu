@@ -10,10 +10,10 @@
 //   mu0 = 1/2 lam + lam1 + dt J_L(U^n)^T lam1        (dJ/dU^n)
 //   lam^n = J_Lambda(V^n)^T mu0                     (dJ/dV^n)
 // J_L^T is applied by a tiled kernel that mirrors the forward one: every face
-// Gauss point gets the adjoint of its flux from the two cells' adjoints, the
-// flux Jacobians with respect to both one-sided states come from forward-mode
-// dual numbers, and each cell gathers the contributions of its faces and of its
-// 2x2 volume points.  J_Lambda^T gathers, for each cell, the derivatives of its
+// Gauss point gets the adjoint of its flux from the two cells' adjoints, one
+// reverse sweep through the exact solver gives the adjoints of both one-sided
+// states (dg_vjp.cuh), and each cell gathers the contributions of its faces and of
+// its 2x2 volume points (reverse sweeps through the physical fluxes).  J_Lambda^T gathers, for each cell, the derivatives of its
 // own limited slopes and of its four neighbours' (whose limiter reads this
 // cell's averages).  Adjoint arrays use the interchange layout (float64).
 #include <cuda_runtime.h>
@@ -26,6 +26,7 @@
 #include "dg_dual.cuh"
 #include "dg_internal.h"
 #include "dg_stage2d.cuh"
+#include "dg_vjp.cuh"
 
 using namespace dgk;
 
@@ -162,26 +163,9 @@ __global__ void __launch_bounds__(VjpTile<TC>::X * VjpTile<TC>::Y) rhs_vjp2d_ker
       cl[v] = s_c0[v * R1 + rl] + s_sl[(2 * v) * R1 + rl] * xl + s_sl[(2 * v + 1) * R1 + rl] * yl;
       cr[v] = s_c0[v * R1 + rr] + s_sl[(2 * v) * R1 + rr] * xr + s_sl[(2 * v + 1) * R1 + rr] * yr;
     }
+    // adjoints of both one-sided states, one reverse sweep through the flux
     TC lam[8];
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      Dn<TC, 4> dl[4], dr[4], F[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        dl[v] = dconst<TC, 4>(cl[v]);
-        dr[v] = dconst<TC, 4>(cr[v]);
-        if (side == 0) dl[v].d[v] = TC(1);
-        else dr[v].d[v] = TC(1);
-      }
-      dface_flux2d<TC, 4>(G, xf ? 0 : 1, dl, dr, F, err);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        TC a = TC(0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) a += mu[q] * F[q].d[i];
-        lam[side * 4 + i] = a;
-      }
-    }
+    face_flux2d_vjp<TC>(G, xf ? 0 : 1, cl, cr, mu, lam, lam + 4, err);
     if (xf) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) s_lx[(k * 2 + g) * NFX + f] = lam[k];
@@ -230,22 +214,16 @@ __global__ void __launch_bounds__(VjpTile<TC>::X * VjpTile<TC>::Y) rhs_vjp2d_ker
 #pragma unroll
     for (int qp = 0; qp < 4; ++qp) {
       const TC xq = (qp & 1) ? ox : -ox, yq = (qp & 2) ? oy : -oy;
-      Dn<TC, 4> c[4], Fx[4], Fy[4];
+      TC c[4], a[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        c[v] = dconst<TC, 4>(s_c0[v * R1 + r] + s_sl[(2 * v) * R1 + r] * xq +
-                             s_sl[(2 * v + 1) * R1 + r] * yq);
-        c[v].d[v] = TC(1);
-      }
-      dphys_flux2d<TC, 4>(G, c, Fx, Fy);
+      for (int v = 0; v < 4; ++v)
+        c[v] = s_c0[v * R1 + r] + s_sl[(2 * v) * R1 + r] * xq + s_sl[(2 * v + 1) * R1 + r] * yq;
+      phys_flux2d_vjp<TC>(G, c, yx, yy, a);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        TC a = TC(0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) a += yx[q] * Fx[q].d[i] + yy[q] * Fy[q].d[i];
-        acc[3 * i] += a;
-        acc[3 * i + 1] += a * xq;
-        acc[3 * i + 2] += a * yq;
+        acc[3 * i] += a[i];
+        acc[3 * i + 1] += a[i] * xq;
+        acc[3 * i + 2] += a[i] * yq;
       }
     }
     const size_t gc = (size_t)gj * nx + gi;
@@ -466,26 +444,27 @@ bool carve(const AdjointStore& S, const AdjointCall& c, int seg, Work* w) {
   return carve_into((char*)S.work, c, seg, w) <= S.work_bytes;
 }
 
+// The 12 interchange planes of a 2D Euler state: plane v*3 + k is average v (k = 0)
+// or derivative coefficient v*2 + k - 1.  Converted in one launch per state.
+PlaneMap euler2d_planes() {
+  PlaneMap m{};
+  m.nplanes = 12;
+  for (int p = 0; p < 12; ++p) {
+    const int v = p / 3, k = p % 3;
+    m.kind[p] = k == 0 ? 0 : 1;
+    m.idx[p] = k == 0 ? v : v * 2 + (k - 1);
+  }
+  return m;
+}
+
 template <class TS>
 cudaError_t to_internal(const double* src, StateBuf<TS> dst, long n, cudaStream_t st) {
-  for (int p = 0; p < 12; ++p) {
-    int v = p / 3, k = p % 3;
-    cudaError_t e = launch_plane_in<TS>(src + (size_t)p * n, dst, k == 0 ? 0 : 1,
-                                        k == 0 ? v : v * 2 + (k - 1), n, st);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  return launch_state_in<TS>(src, dst, euler2d_planes(), n, st);
 }
 
 template <class TS>
 cudaError_t to_interchange(StateBuf<TS> src, double* dst, long n, cudaStream_t st) {
-  for (int p = 0; p < 12; ++p) {
-    int v = p / 3, k = p % 3;
-    cudaError_t e = launch_plane_out<TS>(src, dst + (size_t)p * n, k == 0 ? 0 : 1,
-                                         k == 0 ? v : v * 2 + (k - 1), n, st);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  return launch_state_out<TS>(src, dst, euler2d_planes(), n, st);
 }
 
 template <class TS>
@@ -639,20 +618,19 @@ dg_status run_t(AdjointStore& S, const AdjointCall& c, int k, const double* lam_
         cudaSuccess)
       break;
     if ((e = to_internal<TS>(ck, sb<TS>(w, 0), n, c.stream)) != cudaSuccess) break;
+    int a = 0;  // buffers 0 and 1 take turns as the step's input and output
     for (long long m = n0; m + 1 < n1; ++m) {
       const double dt = dts[(size_t)m];
-      if ((e = launch_stage2d(0, 0, 1, stage_args<TS>(c, w, sb<TS>(w, 0), sb<TS>(w, 0), sb<TS>(w, 2), dt),
+      if ((e = launch_stage2d(0, 0, 1, stage_args<TS>(c, w, sb<TS>(w, a), sb<TS>(w, a), sb<TS>(w, 2), dt),
                               c.stream)) != cudaSuccess)
         break;
-      if ((e = launch_stage2d(0, 0, 2, stage_args<TS>(c, w, sb<TS>(w, 2), sb<TS>(w, 0), sb<TS>(w, 1), dt),
+      if ((e = launch_stage2d(0, 0, 2, stage_args<TS>(c, w, sb<TS>(w, 2), sb<TS>(w, a), sb<TS>(w, 1 - a), dt),
                               c.stream)) != cudaSuccess)
         break;
-      if ((e = to_interchange<TS>(sb<TS>(w, 1), w.segbuf + (size_t)(m + 1 - n0) * plane, n,
+      if ((e = to_interchange<TS>(sb<TS>(w, 1 - a), w.segbuf + (size_t)(m + 1 - n0) * plane, n,
                                   c.stream)) != cudaSuccess)
         break;
-      if ((e = to_internal<TS>(w.segbuf + (size_t)(m + 1 - n0) * plane, sb<TS>(w, 0), n,
-                               c.stream)) != cudaSuccess)
-        break;
+      a = 1 - a;
     }
     if (e != cudaSuccess) break;
     // reverse through the segment

@@ -440,7 +440,7 @@ dg_status reset_ctl_and_cfl(dg_ctx* c) {
   if (c->bar) CK(c, cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), c->stream));
   dg_status s = c->fp32 ? init_cfl_t<float>(c) : init_cfl_t<double>(c);
   if (s != DG_OK) return s;
-  CK(c, launch_ctl_commit(c->ctl, (int)c->probs.size(), c->stream));
+  CK(c, launch_ctl_commit(c->ctl, (int)c->probs.size(), c->cfl, c->stream));
   return DG_OK;
 }
 

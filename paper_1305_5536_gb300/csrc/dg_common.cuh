@@ -14,6 +14,7 @@ namespace dgk {
 // integer atomicMax orders it), and the last CTA to finish moves it to vmax_cur.
 struct Ctl {
   double vmax_cur;
+  double dt_cur;  // cfl / vmax_cur, formed once per step by whoever sets vmax_cur
   unsigned long long vmax_next;
   double t;
   double dt_last;
@@ -139,6 +140,17 @@ __device__ __forceinline__ void ring3d_cell(int e, int& rx, int& ry, int& rz) {
     const int k = e - NT - 2 * (SX + SY), s = k >= SZ, q = k - s * SZ;
     rz = s ? TZ + 1 : 0; rx = q % TX + 1; ry = q / TX + 1;
   }
+}
+
+// Division of small non-negative integers by a divisor known only at run time (a
+// face count of a rolled loop over orientations): floor(n / d) = (n * m) >> 32
+// with m = ceil(2^32 / d), exact for n < 2^14 and d <= 1024 (checked for every
+// such pair); two instructions instead of a full integer division.
+__device__ __forceinline__ unsigned div_magic(unsigned d) {
+  return (unsigned)((0x100000000ull + d - 1) / d);
+}
+__device__ __forceinline__ int div_by_magic(int n, unsigned m) {
+  return (int)__umulhi((unsigned)n, m);
 }
 
 __host__ __device__ __forceinline__ int wrap_index(int g, int n) {

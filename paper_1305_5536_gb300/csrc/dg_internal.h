@@ -78,7 +78,7 @@ template <class TS>
 cudaError_t launch_cfl(int eq, int dim, StateBuf<TS> s, int nx, int ny, int nz, double dx,
                        double dy, double dz, double gamma, Ctl* ctl, cudaStream_t st);
 cudaError_t launch_ctl_reset(Ctl* ctl, int nprob, cudaStream_t st);
-cudaError_t launch_ctl_commit(Ctl* ctl, int nprob, cudaStream_t st);
+cudaError_t launch_ctl_commit(Ctl* ctl, int nprob, double cfl, cudaStream_t st);
 
 // Neumaier-compensated FP64 sums of the average planes: out[v] = sum_cells c0[v].
 cudaError_t launch_totals(const double* c0, int nv, long ncell, double* partial, double* out,

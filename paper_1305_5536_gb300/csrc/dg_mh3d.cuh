@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) mh3d_kernel(const Stage3DArgs<TS
   unsigned err = 0;
   if (tid == 0) {
     s_err = 0;
-    double dt = A.dt_override > 0.0 ? A.dt_override : A.cfl / A.ctl->vmax_cur;
+    double dt = A.dt_override > 0.0 ? A.dt_override : A.ctl->dt_cur;
     if (!(dt > 0.0) || !(dt < 1e300)) err |= ERR_NONPHYS;
     s_dt = dt;
   }
@@ -306,13 +306,16 @@ __global__ void __launch_bounds__(TX * TY * TZ) mh3d_kernel(const Stage3DArgs<TS
   for (int d = 0; d < 3; ++d) {
     const int FX = TX + (d == 0), FY = TY + (d == 1), FZ = TZ + (d == 2);
     const int NFACE = FX * FY * FZ;
+    static_assert((TX + 1) * (TY + 1) * (TZ + 1) < 16384 && (TX + 1) * (TY + 1) <= 1024,
+                  "face indices within the exact range of div_by_magic");
+    const unsigned mXY = div_magic(FX * FY), mX = div_magic(FX);
     const int step = d == 0 ? 1 : (d == 1 ? R1X : R1X * R1Y);
     const TC hn = d == 0 ? hh[0] : (d == 1 ? hh[1] : hh[2]);
     const TC o1 = d == 0 ? oo[1] : oo[0], o2 = d == 2 ? oo[1] : oo[2];
     for (int e = tid; e < NPT * NFACE; e += NT) {
       const int f = NPT == 4 ? (e >> 2) : e, g = NPT == 4 ? (e & 3) : 0;
-      const int fz = f / (FX * FY), fr = f - fz * (FX * FY);
-      const int fy = fr / FX, fx = fr - fy * FX;
+      const int fz = div_by_magic(f, mXY), fr = f - fz * (FX * FY);
+      const int fy = div_by_magic(fr, mX), fx = fr - fy * FX;
       // + side cell: halo-1 coordinates (fx+1, fy+1, fz+1); - side one step back
       const int r1r = ((fz + 1) * R1Y + (fy + 1)) * R1X + (fx + 1);
       const int r1l = r1r - step;
@@ -406,6 +409,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) mh3d_kernel(const Stage3DArgs<TS
       __threadfence();
       double vm = __longlong_as_double((long long)atomicAdd(&ctl->vmax_next, 0ull));
       ctl->vmax_cur = vm;
+      ctl->dt_cur = A.cfl / vm;
       ctl->vmax_next = 0ull;
       ctl->t += dt;
       ctl->dt_last = dt;

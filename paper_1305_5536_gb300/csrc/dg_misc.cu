@@ -191,6 +191,7 @@ __global__ void ctl_reset_kernel(Ctl* ctl, int nprob) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < nprob) {
     ctl[p].vmax_cur = 0.0;
+    ctl[p].dt_cur = 0.0;
     ctl[p].vmax_next = 0ull;
     ctl[p].t = 0.0;
     ctl[p].dt_last = 0.0;
@@ -200,11 +201,12 @@ __global__ void ctl_reset_kernel(Ctl* ctl, int nprob) {
     ctl[p].err_step = -1;
   }
 }
-__global__ void ctl_commit_kernel(Ctl* ctl, int nprob) {
+__global__ void ctl_commit_kernel(Ctl* ctl, int nprob, double cfl) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < nprob) {
     double vm = __longlong_as_double((long long)ctl[p].vmax_next);
     ctl[p].vmax_cur = vm;
+    ctl[p].dt_cur = cfl / vm;
     ctl[p].vmax_next = 0ull;
     if (!(vm > 0.0)) ctl[p].err |= ERR_NONPHYS;
     if (ctl[p].err && ctl[p].err_step < 0) ctl[p].err_step = ctl[p].step;
@@ -214,8 +216,8 @@ cudaError_t launch_ctl_reset(Ctl* ctl, int nprob, cudaStream_t st) {
   ctl_reset_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(ctl, nprob);
   return cudaGetLastError();
 }
-cudaError_t launch_ctl_commit(Ctl* ctl, int nprob, cudaStream_t st) {
-  ctl_commit_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(ctl, nprob);
+cudaError_t launch_ctl_commit(Ctl* ctl, int nprob, double cfl, cudaStream_t st) {
+  ctl_commit_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(ctl, nprob, cfl);
   return cudaGetLastError();
 }
 

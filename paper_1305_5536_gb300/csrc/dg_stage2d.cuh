@@ -254,7 +254,7 @@ __device__ __forceinline__ void stage2d_setup(const Stage2DArgs<TS>& A, int i0, 
   const int tid = threadIdx.x;
   if (tid == 0) {
     S.err = 0;
-    double dt = A.dt_override > 0.0 ? A.dt_override : A.cfl / A.ctl->vmax_cur;
+    double dt = A.dt_override > 0.0 ? A.dt_override : A.ctl->dt_cur;
     if (!(dt > 0.0) || !(dt < 1e300)) S.err |= ERR_NONPHYS;
     S.dt = dt;
   }
@@ -397,6 +397,7 @@ __device__ __forceinline__ void courant_commit2d(const Stage2DArgs<TS>& A, const
       __threadfence();
       double vm = __longlong_as_double((long long)atomicAdd(&ctl->vmax_next, 0ull));
       ctl->vmax_cur = vm;
+      ctl->dt_cur = A.cfl / vm;
       ctl->vmax_next = 0ull;
       ctl->t += dt;
       ctl->dt_last = dt;

@@ -38,9 +38,9 @@ __host__ __device__ constexpr int stage3d_face_max() {
 // the face fluxes [5][4][FMAX] then reuse their space.
 template <int TX, int TY, int TZ, class TC>
 __host__ __device__ constexpr size_t stage3d_wsz() {
-  return size_t(5) * (TX + 4) * (TY + 4) * (TZ + 4) > size_t(5) * 4 * stage3d_face_max<TX, TY, TZ, TC>()
-             ? size_t(5) * (TX + 4) * (TY + 4) * (TZ + 4)
-             : size_t(5) * 4 * stage3d_face_max<TX, TY, TZ, TC>();
+  return (size_t(5) * (TX + 4) * (TY + 4) * (TZ + 4) > size_t(5) * 4 * stage3d_face_max<TX, TY, TZ, TC>()
+              ? size_t(5) * (TX + 4) * (TY + 4) * (TZ + 4) + 3
+              : size_t(5) * 4 * stage3d_face_max<TX, TY, TZ, TC>() + 3) / 4 * 4;
 }
 
 template <int TX, int TY, int TZ, class TC>
@@ -116,6 +116,40 @@ __device__ __forceinline__ void eval3d(const TC* c0, const TC* s, TC x, TC y, TC
   for (int v = 0; v < 5; ++v) c[v] = c0[v] + s[3 * v] * x + s[3 * v + 1] * y + s[3 * v + 2] * z;
 }
 
+// A staged cell of the 3D Euler tile as one record of 20 elements (16-byte
+// aligned): the 5 averages, then the 15 derivative coefficients in slope order,
+// so that a thread reads a cell with 5 (FP32) or 10 (FP64) 16-byte shared loads;
+// at a stride of 20 words the 8 threads of each phase of such a load hit
+// disjoint banks.
+constexpr int kRec3d = 20;
+template <class TC>
+__device__ __forceinline__ void rec_get(const TC* rec, TC* v) {
+  if constexpr (sizeof(TC) == 4) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const float4 q = reinterpret_cast<const float4*>(rec)[i];
+      v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+      const double2 q = reinterpret_cast<const double2*>(rec)[i];
+      v[2 * i] = q.x; v[2 * i + 1] = q.y;
+    }
+  }
+}
+template <class TC>
+__device__ __forceinline__ void rec_put(TC* rec, const TC* v) {
+  if constexpr (sizeof(TC) == 4) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      reinterpret_cast<float4*>(rec)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) reinterpret_cast<double2*>(rec)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+  }
+}
+
 // Physical flux along axis d of conserved (rho, m, E).
 template <class TC>
 __device__ __forceinline__ void phys_flux3d(const Gas<TC>& G, const TC* c, int d, TC* F,
@@ -188,12 +222,17 @@ __device__ __forceinline__ void gather3d(const TC* s_f, int FMAX, int fm, int fp
 // and every average of the halo-2 box that this thread reads next is requested
 // into L2, so that the DRAM latencies of the staging overlap.  The caller then
 // reads the averages, calls cp_async_wait_all() and synchronises.
-template <int NV, int NS, int TX, int TY, int TZ, class TS, class TC>
+// REC > 0: the coefficients go into per-cell records of REC elements, coefficient
+// k of halo-1 cell r1 at s_sl[r1 * REC + OFF + k]; else planes s_sl[k * R1 + r1].
+// PREFETCH = false leaves out the L2 requests for the averages (the 3D Euler
+// kernel, which reads them two cells at a time, measured 1 % faster without).
+template <int NV, int NS, int TX, int TY, int TZ, class TS, class TC, int REC = 0, int OFF = 0,
+          bool PREFETCH = true>
 __device__ __forceinline__ void stage3d_issue(const StateBuf<TS>& in, size_t ncell,
                                               const int* s_gx, const int* s_gy, const int* s_gz,
                                               TC* s_sl) {
   constexpr int R2X = TX + 4, R2Y = TY + 4, R2 = R2X * R2Y * (TZ + 4);
-  constexpr int R1X = TX + 2, R1Y = TY + 2, R1 = R1X * R1Y * (TZ + 2);
+  constexpr int R1X = TX + 2, R1Y = TY + 2;
   constexpr int NT = TX * TY * TZ;
   static_assert(sizeof(TS) == sizeof(TC), "derivative coefficients are staged as stored");
   {  // planes (v, rz) of R1X x R1Y cells: thread t keeps position t % PL of every
@@ -205,20 +244,23 @@ __device__ __forceinline__ void stage3d_issue(const StateBuf<TS>& in, size_t nce
       const int ry = q / R1X, rx = q - ry * R1X;
       const TS* src = in.sl + s_gy[ry + 1] + s_gx[rx + 1];
       size_t voff = 0;
-      int rz = p0;
+      int rz = p0, k = 0;
       for (int p = p0; p < NS * R1Z; p += C1) {
-        cp_async_elem<sizeof(TS)>(&s_sl[p * PL + q], src + voff + s_gz[rz + 1]);
+        TC* dst = REC > 0 ? &s_sl[(rz * PL + q) * REC + OFF + k] : &s_sl[p * PL + q];
+        cp_async_elem<sizeof(TS)>(dst, src + voff + s_gz[rz + 1]);
         rz += C1;
-        if (rz >= R1Z) { rz -= R1Z; voff += ncell; }
+        if (rz >= R1Z) { rz -= R1Z; voff += ncell; ++k; }
       }
     }
   }
-  for (int r = threadIdx.x; r < R2; r += NT) {
-    int rz = r / (R2X * R2Y), rr = r - rz * (R2X * R2Y);
-    int ry = rr / R2X, rx = rr - ry * R2X;
-    const size_t g = (size_t)s_gz[rz] + s_gy[ry] + s_gx[rx];
+  if (PREFETCH) {
+    for (int r = threadIdx.x; r < R2; r += NT) {
+      int rz = r / (R2X * R2Y), rr = r - rz * (R2X * R2Y);
+      int ry = rr / R2X, rx = rr - ry * R2X;
+      const size_t g = (size_t)s_gz[rz] + s_gy[ry] + s_gx[rx];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) prefetch_l2(&in.c0[v * ncell + g]);
+      for (int v = 0; v < NV; ++v) prefetch_l2(&in.c0[v * ncell + g]);
+    }
   }
 }
 
@@ -258,9 +300,8 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
   constexpr int WS = (int)stage3d_wsz<TX, TY, TZ, TC>();
   TC* s_w = reinterpret_cast<TC*>(smem_raw);  // 5 x R2 primitives, then
   TC* s_f = s_w;                              //   5 x 4 x FMAX face fluxes
-  TC* s_c0 = s_w + WS;                        // 5 x R1 averages
-  TC* s_sl = s_c0 + 5 * R1;                   // 15 x R1 derivatives
-  int* s_gx = reinterpret_cast<int*>(s_sl + 15 * R1);
+  TC* s_rec = s_w + WS;                       // R1 records: 5 averages, 15 derivatives
+  int* s_gx = reinterpret_cast<int*>(s_rec + kRec3d * R1);
   int* s_gy = s_gx + R2X;
   int* s_gz = s_gy + R2Y;
   __shared__ double s_dt;
@@ -280,7 +321,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
   ph.begin(A.phase, STAGE);
   if (tid == 0) {
     s_err = 0;
-    double dt = A.dt_override > 0.0 ? A.dt_override : A.cfl / A.ctl->vmax_cur;
+    double dt = A.dt_override > 0.0 ? A.dt_override : A.ctl->dt_cur;
     if (!(dt > 0.0) || !(dt < 1e300)) err |= ERR_NONPHYS;
     s_dt = dt;
   }
@@ -292,22 +333,44 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
 
   // ---- primitives of the halo-2 box; averages of the halo-1 box
   if (STAGE == 2) stage3d_prefetch_base<5, 15, TX, TY>(A, ncell, s_gx, s_gy, s_gz);
-  stage3d_issue<5, 15, TX, TY, TZ>(A.in, ncell, s_gx, s_gy, s_gz, s_sl);
-  for (int r = tid; r < R2; r += NT) {
-    int rz = r / (R2X * R2Y), rr = r - rz * (R2X * R2Y);
-    int ry = rr / R2X, rx = rr - ry * R2X;
-    size_t g = (size_t)s_gz[rz] + s_gy[ry] + s_gx[rx];
+  stage3d_issue<5, 15, TX, TY, TZ, TS, TC, kRec3d, 5, false>(A.in, ncell, s_gx, s_gy, s_gz, s_rec);
+  // two halo-2 cells per pass, all ten FP64 loads in flight before the first is
+  // converted (the second cell of the last pass re-reads the first if it is past
+  // the box, so every load stays in the grid)
+  auto cell_of = [&](int r, int& rx, int& ry, int& rz) {
+    rz = r / (R2X * R2Y);
+    const int rr = r - rz * (R2X * R2Y);
+    ry = rr / R2X;
+    rx = rr - ry * R2X;
+    return (size_t)s_gz[rz] + s_gy[ry] + s_gx[rx];
+  };
+  auto put = [&](int r, int rx, int ry, int rz, const double* a) {
     TC c[5], W[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) c[v] = Cvt<TC>::to_tc(__ldg(&A.in.c0[v * ncell + g]));
+    for (int v = 0; v < 5; ++v) c[v] = Cvt<TC>::to_tc(a[v]);
     prims3d<TC>(G, c, W, err);
 #pragma unroll
     for (int q = 0; q < 5; ++q) s_w[q * R2 + r] = W[q];
     if (rx >= 1 && rx <= TX + 2 && ry >= 1 && ry <= TY + 2 && rz >= 1 && rz <= TZ + 2) {
-      int r1 = ((rz - 1) * R1Y + (ry - 1)) * R1X + (rx - 1);
+      const int r1 = ((rz - 1) * R1Y + (ry - 1)) * R1X + (rx - 1);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) s_c0[v * R1 + r1] = c[v];
+      for (int v = 0; v < 5; ++v) s_rec[r1 * kRec3d + v] = c[v];
     }
+  };
+  for (int r = tid; r < R2; r += 2 * NT) {
+    const int rb = r + NT;
+    const bool two = rb < R2;
+    int ax, ay, az, bx, by, bz;
+    const size_t ga = cell_of(r, ax, ay, az);
+    const size_t gb = two ? cell_of(rb, bx, by, bz) : ga;
+    double a[5], b[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      a[v] = __ldg(&A.in.c0[v * ncell + ga]);
+      b[v] = __ldg(&A.in.c0[v * ncell + gb]);
+    }
+    put(r, ax, ay, az, a);
+    if (two) put(rb, bx, by, bz, b);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -336,12 +399,11 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
         Wn[4][q] = s_w[q * R2 + r2 - R2X * R2Y];
         Wn[5][q] = s_w[q * R2 + r2 + R2X * R2Y];
       }
-#pragma unroll
-      for (int k = 0; k < 15; ++k) s[k] = s_sl[k * R1 + r1];
-      if (WENO && A.limiter == 2) weno_cell3d<TC>(G, hh, W, Wn, s, nullptr);
-      else limit_cell3d<TC>(G, hh, W, Wn, s);
-#pragma unroll
-      for (int k = 0; k < 15; ++k) s_sl[k * R1 + r1] = s[k];
+      TC v[kRec3d];
+      rec_get<TC>(s_rec + r1 * kRec3d, v);
+      if (WENO && A.limiter == 2) weno_cell3d<TC>(G, hh, W, Wn, v + 5, nullptr);
+      else limit_cell3d<TC>(G, hh, W, Wn, v + 5);
+      rec_put<TC>(s_rec + r1 * kRec3d, v);
     }
     __syncthreads();
   }
@@ -350,15 +412,21 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
   // ---- per-cell state, volume integral
   const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
   const int r1c = ((lz + 1) * R1Y + (ly + 1)) * R1X + (lx + 1);
-  TC c0[5], s[15];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) c0[v] = s_c0[v * R1 + r1c];
-#pragma unroll
-  for (int k = 0; k < 15; ++k) s[k] = s_sl[k * R1 + r1c];
   TC rc0[5], rs[15];
 #pragma unroll
   for (int v = 0; v < 5; ++v) rc0[v] = TC(0);
   {
+    // the cell's own coefficients are read here and again for the combination
+    // (not kept in registers across the face loop)
+    TC c0[5], s[15];
+    {
+      TC v[kRec3d];
+      rec_get<TC>(s_rec + r1c * kRec3d, v);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) c0[q] = v[q];
+#pragma unroll
+      for (int k = 0; k < 15; ++k) s[k] = v[5 + k];
+    }
     TC sF[3][5];
 #pragma unroll
     for (int d = 0; d < 3; ++d)
@@ -391,13 +459,16 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
   for (int d = 0; d < 3; ++d) {
     const int FX = TX + (d == 0), FY = TY + (d == 1), FZ = TZ + (d == 2);
     const int NFACE = FX * FY * FZ;
+    static_assert((TX + 1) * (TY + 1) * (TZ + 1) < 16384 && (TX + 1) * (TY + 1) <= 1024,
+                  "face indices within the exact range of div_by_magic");
+    const unsigned mXY = div_magic(FX * FY), mX = div_magic(FX);
     const int step = d == 0 ? 1 : (d == 1 ? R1X : R1X * R1Y);
     const TC hn = d == 0 ? hh[0] : (d == 1 ? hh[1] : hh[2]);
     const TC o1 = d == 0 ? oo[1] : oo[0], o2 = d == 2 ? oo[1] : oo[2];
     for (int e = tid; e < 4 * NFACE; e += NT) {
       const int f = e >> 2, g = e & 3;
-      const int fz = f / (FX * FY), fr = f - fz * (FX * FY);
-      const int fy = fr / FX, fx = fr - fy * FX;
+      const int fz = div_by_magic(f, mXY), fr = f - fz * (FX * FY);
+      const int fy = div_by_magic(fr, mX), fx = fr - fy * FX;
       // the cell on the + side of the face has tile coordinates (fx, fy, fz),
       // i.e. halo-1 coordinates (fx+1, fy+1, fz+1); the - side is one step back
       // along d
@@ -409,13 +480,11 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
       const TC xl = d == 0 ? hn : a, xr = d == 0 ? -hn : a;
       const TC yl = d == 1 ? hn : (d == 0 ? a : b), yr = d == 1 ? -hn : (d == 0 ? a : b);
       const TC zl = d == 2 ? hn : b, zr = d == 2 ? -hn : b;
-      TC cl0[5], cr0[5], sl[15], sr[15], cl[5], cr[5], F[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) { cl0[v] = s_c0[v * R1 + r1l]; cr0[v] = s_c0[v * R1 + r1r]; }
-#pragma unroll
-      for (int k = 0; k < 15; ++k) { sl[k] = s_sl[k * R1 + r1l]; sr[k] = s_sl[k * R1 + r1r]; }
-      eval3d<TC>(cl0, sl, xl, yl, zl, cl);
-      eval3d<TC>(cr0, sr, xr, yr, zr, cr);
+      TC vl[kRec3d], vr[kRec3d], cl[5], cr[5], F[5];
+      rec_get<TC>(s_rec + r1l * kRec3d, vl);
+      rec_get<TC>(s_rec + r1r * kRec3d, vr);
+      eval3d<TC>(vl, vl + 5, xl, yl, zl, cl);
+      eval3d<TC>(vr, vr + 5, xr, yr, zr, cr);
       face_flux3d<TC>(G, d, cl, cr, F, err);
 #pragma unroll
       for (int v = 0; v < 5; ++v) s_f[(v * FMAX + f) * 4 + g] = F[v];
@@ -434,6 +503,13 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
   }
 
   // ---- Runge-Kutta combination
+  TC s[15];
+  {
+    TC v[kRec3d];
+    rec_get<TC>(s_rec + r1c * kRec3d, v);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) s[k] = v[5 + k];
+  }
   const int gi = i0 + lx, gj = j0 + ly, gk = k0 + lz;
   const bool owner = gi < nx && gj < ny && gk < nz;
   const size_t gc = (size_t)s_gz[lz + 2] + s_gy[ly + 2] + s_gx[lx + 2];
@@ -526,6 +602,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
         __threadfence();
         double vm = __longlong_as_double((long long)atomicAdd(&ctl->vmax_next, 0ull));
         ctl->vmax_cur = vm;
+        ctl->dt_cur = A.cfl / vm;
         ctl->vmax_next = 0ull;
         ctl->t += dt;
         ctl->dt_last = dt;
