@@ -33,6 +33,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 512 << 20
+# SM clock of the issue ceiling (the GB300's maximum, also the clock the timed runs
+# hold: their sampled median is recorded in the line's "clocks")
+ISSUE_CLOCK_MHZ = 2070.0
 # steps after which the run restarts from the initial state (each workload has run
 # at least this far from its initial state without a non-physical state)
 RESTART_STEPS = 1000
@@ -338,10 +341,18 @@ def run_gpu(args):
         e = _ncu_entry(kname, wname)
         if e and "issue_active_pct" in e:
             # the kernels are bound by instruction issue, not by DRAM: the ncu
-            # figures of the same kernel on the same sources
+            # figures of the same kernel on the same sources, and the thread-
+            # instruction rate of this run against the issue ceiling of the part
+            # (152 SMs x 4 schedulers x 32 lanes x the SM clock)
             out["issue"] = {key: e[key] for key in ("issue_active_pct", "pipe_pct",
-                                                      "inst_per_cell", "captured")
+                                                      "thread_inst_per_cell", "lane_efficiency",
+                                                      "captured")
                             if key in e}
+            if "thread_inst_per_launch" in e:
+                rate = e["thread_inst_per_launch"] / (avg_ms * 1e-3)
+                peak = 152 * 4 * 32 * ISSUE_CLOCK_MHZ * 1e6
+                out["issue"].update({"achieved_thread_inst_per_s": rate,
+                                     "peak_thread_inst_per_s": peak, "frac": rate / peak})
         return kname, out
 
     def fp32_accuracy():
