@@ -140,7 +140,7 @@ def test_batch_many_tiles_per_cta_matches_oracle(prec, tol, monkeypatch):
 
 
 def test_batch_workload_of_64_problems_one_step():
-    """The batched workload itself (64 problems, N log-uniform in [32, 512], 3.45 M
+    """The batched workload itself (64 problems, N log-uniform in [32, 512], 3.39 M
     cells, about 13.5 k tiles: every CTA of the cooperative grid walks many tiles),
     FP32, one step with each problem's own Courant time step; a dozen problems are
     compared whole with the oracle, and every problem's time step with the
