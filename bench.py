@@ -11,7 +11,9 @@ every timed step because the 512^2 state fits in L2.  Every RESTART_STEPS steps
 (fewer for workloads whose flow reaches a state the method as stated cannot
 step sooner) the solver restarts from the initial state, which stays resident on
 the device; the restart lies outside the timed events.  Kernel durations come from
-CUDA events the library records around each stage-kernel launch.  Multi-GPU
+CUDA events the library records around each stage-kernel launch, in K more steps
+right after the timed ones (an event between the two stage kernels of a step
+serialises them; the timed steps let the second start while the first drains).  Multi-GPU
 (--gpus N under torchrun): independent replicas, one per rank (weak scaling),
 barrier + max over ranks.  The default workload's line also carries the adjoint
 step time (the checkpointed adjoint of 100 steps of a 2D Euler 256^2 problem,
@@ -270,7 +272,6 @@ def run_gpu(args):
             restart_if_due()
             s.step(1)
         s.sync()
-        s.profile(True)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(K)]
         barrier()
@@ -288,11 +289,21 @@ def run_gpu(args):
             evs[k][1].record(stream)
         barrier()
         t_wall = time.perf_counter() - t_wall
+        # the kernel durations: K more steps with the library's events around each
+        # stage-kernel launch (an event between the two stage kernels of a step
+        # serialises them, so these steps are not the ones whose time is the value)
+        s.profile(True)
+        for k in range(K):
+            flush.fill_(float(k))
+            restart_if_due()
+            s.step(1)
+        s.sync()
+        barrier()
+        t_both = time.perf_counter() - t_start
         if sampler:
-            sampler.window = (t_start, t_start + t_wall)
+            sampler.window = (t_start, t_start + t_both)
             time.sleep(0.2)
             sampler.__exit__()
-        s.sync()
         step_ms = [a.elapsed_time(b) for a, b in evs]
         kms, kn = s.profile_read()
         s.profile(False)

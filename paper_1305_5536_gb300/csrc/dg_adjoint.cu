@@ -55,13 +55,13 @@ __global__ void limit2d_kernel(StateBuf<TS> V, StateBuf<TS> U, int nx, int ny, d
     TC cc[4], W[4], Wn[4][4], s[8];
     unsigned err = 0;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) cc[v] = (TC)V.c0[v * ncell + c];
+    for (int v = 0; v < 4; ++v) cc[v] = Cvt<TC>::to_tc(V.c0[v * ncell + c]);
     prims2d<0, TC>(G, cc, W, err);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       TC cn[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) cn[v] = (TC)V.c0[v * ncell + nb[k]];
+      for (int v = 0; v < 4; ++v) cn[v] = Cvt<TC>::to_tc(V.c0[v * ncell + nb[k]]);
       prims2d<0, TC>(G, cn, Wn[k], err);
     }
 #pragma unroll
@@ -113,11 +113,11 @@ __global__ void __launch_bounds__(VjpTile<TC>::X * VjpTile<TC>::Y) rhs_vjp2d_ker
     int ry = r / R1X, rx = r - ry * R1X;
     size_t g = (size_t)s_gy[ry] + s_gx[rx];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) s_c0[v * R1 + r] = (TC)U.c0[v * ncell + g];
+    for (int v = 0; v < 4; ++v) s_c0[v * R1 + r] = Cvt<TC>::to_tc(U.c0[v * ncell + g]);
 #pragma unroll
     for (int k = 0; k < 8; ++k) s_sl[k * R1 + r] = (TC)U.sl[k * ncell + g];
 #pragma unroll
-    for (int p = 0; p < 12; ++p) s_y[p * R1 + r] = (TC)A.y[p * ncell + g];
+    for (int p = 0; p < 12; ++p) s_y[p * R1 + r] = Cvt<TC>::to_tc(A.y[p * ncell + g]);
   }
   __syncthreads();
 
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(VjpTile<TC>::X * VjpTile<TC>::Y) rhs_vjp2d_ker
     const size_t gc = (size_t)gj * nx + gi;
 #pragma unroll
     for (int p = 0; p < 12; ++p) {
-      double o = A.a1 * A.x1[p * ncell + gc] + A.beta * (double)acc[p];
+      double o = A.a1 * A.x1[p * ncell + gc] + A.beta * Cvt<TC>::to_f64(acc[p]);
       if (A.x2) o += A.a2 * A.x2[p * ncell + gc];
       A.out[p * ncell + gc] = o;
     }
@@ -256,14 +256,14 @@ __global__ void limit_vjp2d_kernel(StateBuf<TS> V, const double* __restrict__ nu
     };
     auto load_c0 = [&](long cell, TC* o) {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) o[v] = (TC)V.c0[v * ncell + cell];
+      for (int v = 0; v < 4; ++v) o[v] = Cvt<TC>::to_tc(V.c0[v * ncell + cell]);
     };
     TC acc[12];
 #pragma unroll
     for (int p = 0; p < 12; ++p) acc[p] = TC(0);
     // averages pass through the limiter unchanged
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[3 * v] = (TC)nu[(3 * v) * ncell + c];
+    for (int v = 0; v < 4; ++v) acc[3 * v] = Cvt<TC>::to_tc(nu[(3 * v) * ncell + c]);
     const int ofs[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
     // (a) this cell's own limiter: derivatives with respect to its averages and
     //     its derivative coefficients (three passes of four directions)
@@ -276,8 +276,8 @@ __global__ void limit_vjp2d_kernel(StateBuf<TS> V, const double* __restrict__ nu
       for (int k = 0; k < 4; ++k) load_c0(at(ofs[k][0], ofs[k][1]), cnv[k]);
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        nus[2 * v] = (TC)nu[(3 * v + 1) * ncell + c];
-        nus[2 * v + 1] = (TC)nu[(3 * v + 2) * ncell + c];
+        nus[2 * v] = Cvt<TC>::to_tc(nu[(3 * v + 1) * ncell + c]);
+        nus[2 * v + 1] = Cvt<TC>::to_tc(nu[(3 * v + 2) * ncell + c]);
       }
 #pragma unroll
       for (int pass = 0; pass < 3; ++pass) {
@@ -322,8 +322,8 @@ __global__ void limit_vjp2d_kernel(StateBuf<TS> V, const double* __restrict__ nu
       for (int q = 0; q < 8; ++q) sv[q] = (TC)V.sl[q * ncell + e];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        nus[2 * v] = (TC)nu[(3 * v + 1) * ncell + e];
-        nus[2 * v + 1] = (TC)nu[(3 * v + 2) * ncell + e];
+        nus[2 * v] = Cvt<TC>::to_tc(nu[(3 * v + 1) * ncell + e]);
+        nus[2 * v + 1] = Cvt<TC>::to_tc(nu[(3 * v + 2) * ncell + e]);
       }
       D c0[4], cn[4][4], s[8];
 #pragma unroll
@@ -351,7 +351,7 @@ __global__ void limit_vjp2d_kernel(StateBuf<TS> V, const double* __restrict__ nu
       }
     }
 #pragma unroll
-    for (int p = 0; p < 12; ++p) out[p * ncell + c] = (double)acc[p];
+    for (int p = 0; p < 12; ++p) out[p * ncell + c] = Cvt<TC>::to_f64(acc[p]);
   }
 }
 

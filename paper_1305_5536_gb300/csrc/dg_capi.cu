@@ -1016,17 +1016,31 @@ dg_status dg_record(dg_ctx* c, int nsteps, double dt_override, double* t_out) {
   h.hist_cap = c->adj.cap_steps;
   h.step = c->adj.nrec;
   CK(c, cudaMemcpyAsync(c->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream));
-  for (int n = 0; n < nsteps; ++n) {
+  const double dtov = dt_override > 0.0 ? dt_override : 0.0;
+  for (int n = 0; n < nsteps;) {
     long long k = c->adj.nrec;
     if (k % c->ckpt_every == 0) {
       double* ck = c->adj.ckpt + (size_t)(k / c->ckpt_every) * c->nplanes * p.ncell;
       dg_status g = c->fp32 ? get_state_t<float>(c, ck, 1) : get_state_t<double>(c, ck, 1);
       if (g != DG_OK) return g;
     }
-    double dtov = dt_override > 0.0 ? dt_override : 0.0;
-    CK(c, launch_step(c, c->cur, c->nxt, dtov));
-    std::swap(c->cur, c->nxt);
-    c->adj.nrec++;
+    // the steps up to the next checkpoint: pairs as the two-step graph, which
+    // writes the same time-step history as single launches (the history index
+    // lives in the control block on the device)
+    const int run = (int)std::min<long long>(nsteps - n, c->ckpt_every - k % c->ckpt_every);
+    int done = 0;
+    if (!c->prof && run >= 2) {
+      cudaGraphExec_t ex;
+      dg_status g = ensure_graph(c, dtov, &ex);
+      if (g != DG_OK) return g;
+      for (; done + 2 <= run; done += 2) CK(c, cudaGraphLaunch(ex, c->stream));
+    }
+    for (; done < run; ++done) {
+      CK(c, launch_step(c, c->cur, c->nxt, dtov));
+      std::swap(c->cur, c->nxt);
+    }
+    c->adj.nrec += run;
+    n += run;
   }
   if (nsteps > 0) c->adj.generation++;
   CK(c, cudaMemcpyAsync(&h, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));

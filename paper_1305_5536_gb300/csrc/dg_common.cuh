@@ -142,6 +142,39 @@ __device__ __forceinline__ void ring3d_cell(int e, int& rx, int& ry, int& rz) {
   }
 }
 
+// The cells of the halo-2 box whose centroid primitives the limiter of the tile
+// and its face slabs reads: the halo-1 box and, beyond each face of the tile, one
+// more layer of the tile's extent (the outer neighbours of the slabs).  Cell e
+// (0 <= e < halo3d_count) as halo-2 box coordinates (rx, ry, rz): first the halo-1
+// box in its own row-major order (so e is the cell's halo-1 index), then the x, y
+// and z layers (low side, then high side).
+template <int TX, int TY, int TZ>
+__host__ __device__ constexpr int halo3d_count() {
+  return (TX + 2) * (TY + 2) * (TZ + 2) + 2 * (TY * TZ + TX * TZ + TX * TY);
+}
+template <int TX, int TY, int TZ>
+__device__ __forceinline__ void halo3d_cell(int e, int& rx, int& ry, int& rz) {
+  constexpr int R1X = TX + 2, R1Y = TY + 2, R1 = R1X * R1Y * (TZ + 2);
+  constexpr int SX = TY * TZ, SY = TX * TZ, SZ = TX * TY;
+  if (e < R1) {
+    rz = e / (R1X * R1Y);
+    const int q = e - rz * (R1X * R1Y);
+    ry = q / R1X;
+    rx = q - ry * R1X + 1;
+    ry += 1;
+    rz += 1;
+  } else if (e < R1 + 2 * SX) {
+    const int k = e - R1, s = k >= SX, q = k - s * SX;
+    rx = s ? TX + 3 : 0; ry = q % TY + 2; rz = q / TY + 2;
+  } else if (e < R1 + 2 * (SX + SY)) {
+    const int k = e - R1 - 2 * SX, s = k >= SY, q = k - s * SY;
+    ry = s ? TY + 3 : 0; rx = q % TX + 2; rz = q / TX + 2;
+  } else {
+    const int k = e - R1 - 2 * (SX + SY), s = k >= SZ, q = k - s * SZ;
+    rz = s ? TZ + 3 : 0; rx = q % TX + 2; ry = q / TX + 2;
+  }
+}
+
 // Division of small non-negative integers by a divisor known only at run time (a
 // face count of a rolled loop over orientations): floor(n / d) = (n * m) >> 32
 // with m = ceil(2^32 / d), exact for n < 2^14 and d <= 1024 (checked for every
@@ -156,6 +189,36 @@ __device__ __forceinline__ int div_by_magic(int n, unsigned m) {
 __host__ __device__ __forceinline__ int wrap_index(int g, int n) {
   int r = g % n;
   return r < 0 ? r + n : r;
+}
+
+// Programmatic dependent launch: a kernel launched with the programmatic stream-
+// serialisation attribute may be scheduled while the kernel before it on the stream
+// is finishing.  griddep_wait() returns once that kernel has completed and its
+// writes are visible (at once for a normal launch); griddep_launch_dependents() lets
+// the launch of the next kernel on the stream begin.
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+// Launch of a stage kernel as a programmatic dependent of the kernel before it on
+// the stream (the kernel must begin with griddep_wait()).
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
 }
 
 // Global -> shared copy of one 4- or 8-byte element without a register round

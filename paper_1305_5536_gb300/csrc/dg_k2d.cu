@@ -27,9 +27,8 @@ static cudaError_t launch2d_w(int stage, const Stage2DArgs<TS>& a, cudaStream_t 
     attr_set = true;
   }
   dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
-  if (stage == 1) stage2d_kernel<EQ, TC, TS, TX, TY, 1, WENO><<<grid, TX * TY, smem, st>>>(a);
-  else stage2d_kernel<EQ, TC, TS, TX, TY, 2, WENO><<<grid, TX * TY, smem, st>>>(a);
-  return cudaGetLastError();
+  if (stage == 1) return launch_pdl(stage2d_kernel<EQ, TC, TS, TX, TY, 1, WENO>, grid, TX * TY, smem, st, a);
+  return launch_pdl(stage2d_kernel<EQ, TC, TS, TX, TY, 2, WENO>, grid, TX * TY, smem, st, a);
 }
 
 // The WENO-type limiter only in the instantiation that needs it.

@@ -21,9 +21,8 @@ static cudaError_t launch3d_w(int stage, const Stage3DArgs<TS>& a, cudaStream_t 
     attr_set = true;
   }
   dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + TZ - 1) / TZ);
-  if (stage == 1) stage3d_kernel<TC, TS, TX, TY, TZ, 1, WENO><<<grid, TX * TY * TZ, smem, st>>>(a);
-  else stage3d_kernel<TC, TS, TX, TY, TZ, 2, WENO><<<grid, TX * TY * TZ, smem, st>>>(a);
-  return cudaGetLastError();
+  if (stage == 1) return launch_pdl(stage3d_kernel<TC, TS, TX, TY, TZ, 1, WENO>, grid, TX * TY * TZ, smem, st, a);
+  return launch_pdl(stage3d_kernel<TC, TS, TX, TY, TZ, 2, WENO>, grid, TX * TY * TZ, smem, st, a);
 }
 
 // The WENO-type limiter only in the instantiation that needs it.

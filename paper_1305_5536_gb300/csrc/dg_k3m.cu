@@ -21,9 +21,8 @@ static cudaError_t launch3m_t(int stage, const Stage3DArgs<TS>& a, cudaStream_t 
     attr_set = true;
   }
   dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + TZ - 1) / TZ);
-  if (stage == 1) stage3m_kernel<TC, TS, TX, TY, TZ, 1, WENO><<<grid, TX * TY * TZ, smem, st>>>(a);
-  else stage3m_kernel<TC, TS, TX, TY, TZ, 2, WENO><<<grid, TX * TY * TZ, smem, st>>>(a);
-  return cudaGetLastError();
+  if (stage == 1) return launch_pdl(stage3m_kernel<TC, TS, TX, TY, TZ, 1, WENO>, grid, TX * TY * TZ, smem, st, a);
+  return launch_pdl(stage3m_kernel<TC, TS, TX, TY, TZ, 2, WENO>, grid, TX * TY * TZ, smem, st, a);
 }
 
 template <class TC, class TS, int TX, int TY, int TZ>

@@ -18,8 +18,7 @@ static cudaError_t launch_mh2d_t(const Stage2DArgs<TS>& a, cudaStream_t st) {
     attr_set = true;
   }
   dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
-  mh2d_kernel<EQ, TC, TS, TX, TY, NGF, WENO><<<grid, TX * TY, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(mh2d_kernel<EQ, TC, TS, TX, TY, NGF, WENO>, grid, TX * TY, smem, st, a);
 }
 
 template <int EQ, class TC, class TS, int TX, int TY>

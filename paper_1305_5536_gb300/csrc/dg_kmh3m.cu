@@ -18,8 +18,7 @@ static cudaError_t launch_mh3m_t(const Stage3DArgs<TS>& a, cudaStream_t st) {
     attr_set = true;
   }
   dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + TZ - 1) / TZ);
-  mh3m_kernel<TC, TS, TX, TY, TZ, NGF, WENO><<<grid, TX * TY * TZ, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(mh3m_kernel<TC, TS, TX, TY, TZ, NGF, WENO>, grid, TX * TY * TZ, smem, st, a);
 }
 
 template <class TC, class TS, int TX, int TY, int TZ>

@@ -418,6 +418,8 @@ __device__ __forceinline__ void mh2d_compute(const Stage2DArgs<TS>& A, int i0, i
 
 template <int EQ, class TC, class TS, int TX, int TY, int NGF, bool WENO>
 __global__ void __launch_bounds__(TX * TY) mh2d_kernel(const Stage2DArgs<TS> A) {
+  griddep_launch_dependents();  // programmatic dependent launch: see griddep_wait()
+  griddep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ TileScalars<TX * TY> S;
   const MhMem2D<TC> M = mh2d_mem<EQ, TX, TY, NGF, TC>(smem_raw);

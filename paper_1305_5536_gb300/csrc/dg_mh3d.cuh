@@ -178,6 +178,8 @@ __device__ __forceinline__ void gather3d_centroid(const TC* s_f, int FMAX, int f
 
 template <class TC, class TS, int TX, int TY, int TZ, int NGF, bool WENO>
 __global__ void __launch_bounds__(TX * TY * TZ) mh3d_kernel(const Stage3DArgs<TS> A) {
+  griddep_launch_dependents();  // programmatic dependent launch: see griddep_wait()
+  griddep_wait();
   constexpr int R2X = TX + 4, R2Y = TY + 4, R2Z = TZ + 4, R2 = R2X * R2Y * R2Z;
   constexpr int R1X = TX + 2, R1Y = TY + 2, R1Z = TZ + 2, R1 = R1X * R1Y * R1Z;
   constexpr int NT = TX * TY * TZ;

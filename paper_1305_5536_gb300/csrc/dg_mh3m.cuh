@@ -155,6 +155,8 @@ __device__ __forceinline__ void prim_flux3m(const Gas<TC>& G, const TC* W, int d
 
 template <class TC, class TS, int TX, int TY, int TZ, int NGF, bool WENO>
 __global__ void __launch_bounds__(TX * TY * TZ) mh3m_kernel(const Stage3DArgs<TS> A) {
+  griddep_launch_dependents();  // programmatic dependent launch: see griddep_wait()
+  griddep_wait();
   constexpr int R2X = TX + 4, R2Y = TY + 4, R2Z = TZ + 4, R2 = R2X * R2Y * R2Z;
   constexpr int R1X = TX + 2, R1Y = TY + 2, R1Z = TZ + 2, R1 = R1X * R1Y * R1Z;
   constexpr int NT = TX * TY * TZ;

@@ -684,6 +684,10 @@ template <int EQ, class TC, class TS, int TX, int TY, int STAGE, bool WENO>
 __global__ void __launch_bounds__(TX * TY, (StageMinBlocks<TX * TY, TC>::v))
     stage2d_kernel(const Stage2DArgs<TS> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // launched as a programmatic dependent of the previous stage: everything of the
+  // tile reads that stage's output, so wait for it before anything else
+  griddep_launch_dependents();
+  griddep_wait();
   stage2d_tile<EQ, TC, TS, TX, TY, STAGE, WENO>(A, blockIdx.x * TX, blockIdx.y * TY,
                                           gridDim.x * gridDim.y, smem_raw);
 }

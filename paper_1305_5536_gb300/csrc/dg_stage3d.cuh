@@ -3,8 +3,9 @@
 // fused kernel.
 //
 // One CTA owns a TX x TY x TZ tile.  Shared memory holds the centroid primitives
-// of the tile plus a halo of 2 cells (for the limiter's neighbour extrema), the
-// averages and derivative coefficients of the tile plus a halo of 1 cell, and one
+// of the cells the limiter's neighbour extrema read (the tile plus a halo of 1
+// cell, and one more layer beyond each face of the tile), the averages and
+// derivative coefficients of the tile plus a halo of 1 cell, and one
 // face-flux buffer.  After the limiter (Sec. 2.5) has been applied in place to the
 // tile and its ring, the faces of each orientation are processed in turn: the
 // Riemann flux at the 2x2 Gauss points of every face of that orientation is
@@ -34,8 +35,8 @@ __host__ __device__ constexpr int stage3d_face_max() {
                                                           : TX * TY * (TZ + 1));
 }
 
-// The primitives of the halo-2 box [5][R2] are dead once the limiter has run;
-// the face fluxes [5][4][FMAX] then reuse their space.
+// The primitives (laid out as the halo-2 box [5][R2], of which the cells of
+// halo3d_cell are written) are dead once the limiter has run; the face fluxes [5][4][FMAX] then reuse their space.
 template <int TX, int TY, int TZ, class TC>
 __host__ __device__ constexpr size_t stage3d_wsz() {
   return (size_t(5) * (TX + 4) * (TY + 4) * (TZ + 4) > size_t(5) * 4 * stage3d_face_max<TX, TY, TZ, TC>()
@@ -225,9 +226,11 @@ __device__ __forceinline__ void gather3d(const TC* s_f, int FMAX, int fm, int fp
 // REC > 0: the coefficients go into per-cell records of REC elements, coefficient
 // k of halo-1 cell r1 at s_sl[r1 * REC + OFF + k]; else planes s_sl[k * R1 + r1].
 // PREFETCH = false leaves out the L2 requests for the averages (the 3D Euler
-// kernel, which reads them two cells at a time, measured 1 % faster without).
+// kernel, which reads them two cells at a time, measured 1 % faster without);
+// HALO = true requests only the cells of halo3d_cell, the ones a kernel whose
+// limiter covers the tile and its face slabs reads.
 template <int NV, int NS, int TX, int TY, int TZ, class TS, class TC, int REC = 0, int OFF = 0,
-          bool PREFETCH = true>
+          bool PREFETCH = true, bool HALO = false>
 __device__ __forceinline__ void stage3d_issue(const StateBuf<TS>& in, size_t ncell,
                                               const int* s_gx, const int* s_gy, const int* s_gz,
                                               TC* s_sl) {
@@ -254,9 +257,16 @@ __device__ __forceinline__ void stage3d_issue(const StateBuf<TS>& in, size_t nce
     }
   }
   if (PREFETCH) {
-    for (int r = threadIdx.x; r < R2; r += NT) {
-      int rz = r / (R2X * R2Y), rr = r - rz * (R2X * R2Y);
-      int ry = rr / R2X, rx = rr - ry * R2X;
+    for (int r = threadIdx.x; r < (HALO ? halo3d_count<TX, TY, TZ>() : R2); r += NT) {
+      int rx, ry, rz;
+      if (HALO) {
+        halo3d_cell<TX, TY, TZ>(r, rx, ry, rz);
+      } else {
+        rz = r / (R2X * R2Y);
+        const int rr = r - rz * (R2X * R2Y);
+        ry = rr / R2X;
+        rx = rr - ry * R2X;
+      }
       const size_t g = (size_t)s_gz[rz] + s_gy[ry] + s_gx[rx];
 #pragma unroll
       for (int v = 0; v < NV; ++v) prefetch_l2(&in.c0[v * ncell + g]);
@@ -290,6 +300,8 @@ struct Stage3dMinBlocks {
 template <class TC, class TS, int TX, int TY, int TZ, int STAGE, bool WENO>
 __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, TC>::v))
     stage3d_kernel(const Stage3DArgs<TS> A) {
+  griddep_launch_dependents();  // programmatic dependent launch: see griddep_wait()
+  griddep_wait();
   constexpr int R2X = TX + 4, R2Y = TY + 4, R2Z = TZ + 4, R2 = R2X * R2Y * R2Z;
   constexpr int R1X = TX + 2, R1Y = TY + 2, R1Z = TZ + 2, R1 = R1X * R1Y * R1Z;
   constexpr int NT = TX * TY * TZ;
@@ -331,46 +343,47 @@ __global__ void __launch_bounds__(TX * TY * TZ, (Stage3dMinBlocks<TX * TY * TZ, 
     s_gz[tid - R2X - R2Y] = wrap_index(k0 - 2 + (tid - R2X - R2Y), nz) * nx * ny;
   __syncthreads();
 
-  // ---- primitives of the halo-2 box; averages of the halo-1 box
+  // ---- primitives where the limiter reads them; averages of the halo-1 box
   if (STAGE == 2) stage3d_prefetch_base<5, 15, TX, TY>(A, ncell, s_gx, s_gy, s_gz);
   stage3d_issue<5, 15, TX, TY, TZ, TS, TC, kRec3d, 5, false>(A.in, ncell, s_gx, s_gy, s_gz, s_rec);
-  // two halo-2 cells per pass, all ten FP64 loads in flight before the first is
+  // the halo-2 cells the limiter reads (the halo-1 box and the six outer face
+  // layers), two per pass, all ten FP64 loads in flight before the first is
   // converted (the second cell of the last pass re-reads the first if it is past
-  // the box, so every load stays in the grid)
-  auto cell_of = [&](int r, int& rx, int& ry, int& rz) {
-    rz = r / (R2X * R2Y);
-    const int rr = r - rz * (R2X * R2Y);
-    ry = rr / R2X;
-    rx = rr - ry * R2X;
+  // the set, so every load stays in the grid)
+  constexpr int NH = halo3d_count<TX, TY, TZ>();
+  auto cell_of = [&](int e, int& r, int& r1ok) {
+    int rx, ry, rz;
+    halo3d_cell<TX, TY, TZ>(e, rx, ry, rz);
+    r = (rz * R2Y + ry) * R2X + rx;
+    r1ok = e < R1;
     return (size_t)s_gz[rz] + s_gy[ry] + s_gx[rx];
   };
-  auto put = [&](int r, int rx, int ry, int rz, const double* a) {
+  auto put = [&](int e, int r, int r1ok, const double* a) {
     TC c[5], W[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) c[v] = Cvt<TC>::to_tc(a[v]);
     prims3d<TC>(G, c, W, err);
 #pragma unroll
     for (int q = 0; q < 5; ++q) s_w[q * R2 + r] = W[q];
-    if (rx >= 1 && rx <= TX + 2 && ry >= 1 && ry <= TY + 2 && rz >= 1 && rz <= TZ + 2) {
-      const int r1 = ((rz - 1) * R1Y + (ry - 1)) * R1X + (rx - 1);
+    if (r1ok) {  // e is the cell's halo-1 index
 #pragma unroll
-      for (int v = 0; v < 5; ++v) s_rec[r1 * kRec3d + v] = c[v];
+      for (int v = 0; v < 5; ++v) s_rec[e * kRec3d + v] = c[v];
     }
   };
-  for (int r = tid; r < R2; r += 2 * NT) {
-    const int rb = r + NT;
-    const bool two = rb < R2;
-    int ax, ay, az, bx, by, bz;
-    const size_t ga = cell_of(r, ax, ay, az);
-    const size_t gb = two ? cell_of(rb, bx, by, bz) : ga;
+  for (int e = tid; e < NH; e += 2 * NT) {
+    const int eb = e + NT;
+    const bool two = eb < NH;
+    int ra, rb, oka, okb;
+    const size_t ga = cell_of(e, ra, oka);
+    const size_t gb = two ? cell_of(eb, rb, okb) : ga;
     double a[5], b[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       a[v] = __ldg(&A.in.c0[v * ncell + ga]);
       b[v] = __ldg(&A.in.c0[v * ncell + gb]);
     }
-    put(r, ax, ay, az, a);
-    if (two) put(rb, bx, by, bz, b);
+    put(e, ra, oka, a);
+    if (two) put(eb, rb, okb, b);
   }
   cp_async_wait_all();
   __syncthreads();

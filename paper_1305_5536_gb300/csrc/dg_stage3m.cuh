@@ -9,9 +9,10 @@
 //   Bx = b1 + (a10 + a11) x + a4 y + a5 z,
 //   By = b2 + a6 x - a10 y + a7 z,
 //   Bz = b3 + a8 x + a9 y - a11 z.
-// The tile is processed as in dg_stage3d.cuh: primitives of the halo-2 box, the
-// min/max limiter on the halo-1 box (one factor for the whole field, so every
-// cell stays divergence free), the volume integral at the 8 Gauss points, and
+// The tile is processed as in dg_stage3d.cuh: primitives of the cells the limiter
+// reads, the min/max limiter on the tile and its face slabs (one factor for the
+// whole field, so every cell stays divergence free), the volume integral at the
+// 8 Gauss points, and
 // the faces one orientation at a time (HLLD with two transverse components and
 // the averaged normal field of Sec. 2.6, at the 2x2 Gauss points), gathered by
 // both cells.
@@ -31,8 +32,8 @@
 
 namespace dgk {
 
-// The primitives of the halo-2 box [8][R2] are dead once the limiter has run;
-// the face fluxes [8][4][FMAX] then reuse their space.
+// The primitives (laid out as the halo-2 box [8][R2]) are dead once the limiter
+// has run; the face fluxes [8][4][FMAX] then reuse their space.
 template <int TX, int TY, int TZ, class TC>
 __host__ __device__ constexpr size_t stage3m_wsz() {
   return size_t(8) * (TX + 4) * (TY + 4) * (TZ + 4) > size_t(8) * 4 * stage3d_face_max<TX, TY, TZ, TC>()
@@ -326,8 +327,18 @@ __device__ __forceinline__ void field_rhs3m(const TC* rs24, const TC* hd, TC* ra
   ra[7] = (A * Q - hx2 * P) / det;
 }
 
+// FP32: two resident 256-thread CTAs per SM (128 registers a thread); FP64 keeps
+// its registers.
+template <int NT, class TC>
+struct Stage3mMinBlocks {
+  static constexpr int v = sizeof(TC) == 4 && 65536 / (128 * NT) > 0 ? 65536 / (128 * NT) : 1;
+};
+
 template <class TC, class TS, int TX, int TY, int TZ, int STAGE, bool WENO>
-__global__ void __launch_bounds__(TX * TY * TZ) stage3m_kernel(const Stage3DArgs<TS> A) {
+__global__ void __launch_bounds__(TX * TY * TZ, (Stage3mMinBlocks<TX * TY * TZ, TC>::v))
+    stage3m_kernel(const Stage3DArgs<TS> A) {
+  griddep_launch_dependents();  // programmatic dependent launch: see griddep_wait()
+  griddep_wait();
   constexpr int R2X = TX + 4, R2Y = TY + 4, R2Z = TZ + 4, R2 = R2X * R2Y * R2Z;
   constexpr int R1X = TX + 2, R1Y = TY + 2, R1Z = TZ + 2, R1 = R1X * R1Y * R1Z;
   constexpr int NT = TX * TY * TZ;
@@ -366,12 +377,16 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3m_kernel(const Stage3DArgs
     s_gz[tid - R2X - R2Y] = wrap_index(k0 - 2 + (tid - R2X - R2Y), nz) * nx * ny;
   __syncthreads();
 
-  // ---- primitives of the halo-2 box; averages of the halo-1 box
+  // ---- primitives where the limiter reads them; averages of the halo-1 box
   if (STAGE == 2) stage3d_prefetch_base<8, 23, TX, TY>(A, ncell, s_gx, s_gy, s_gz);
-  stage3d_issue<8, 23, TX, TY, TZ>(A.in, ncell, s_gx, s_gy, s_gz, s_sl);
-  for (int r = tid; r < R2; r += NT) {
-    int rz = r / (R2X * R2Y), rr = r - rz * (R2X * R2Y);
-    int ry = rr / R2X, rx = rr - ry * R2X;
+  stage3d_issue<8, 23, TX, TY, TZ, TS, TC, 0, 0, true, true>(A.in, ncell, s_gx, s_gy, s_gz, s_sl);
+  // the halo-2 cells the limiter reads: the halo-1 box, then the six outer face
+  // layers (e < R1 is the cell's halo-1 index)
+#pragma unroll 1
+  for (int e = tid; e < halo3d_count<TX, TY, TZ>(); e += NT) {
+    int rx, ry, rz;
+    halo3d_cell<TX, TY, TZ>(e, rx, ry, rz);
+    const int r = (rz * R2Y + ry) * R2X + rx;
     size_t g = (size_t)s_gz[rz] + s_gy[ry] + s_gx[rx];
     TC c[8], W[8];
 #pragma unroll
@@ -379,10 +394,9 @@ __global__ void __launch_bounds__(TX * TY * TZ) stage3m_kernel(const Stage3DArgs
     prims3m<TC>(G, c, W, err);
 #pragma unroll
     for (int q = 0; q < 8; ++q) s_w[q * R2 + r] = W[q];
-    if (rx >= 1 && rx <= TX + 2 && ry >= 1 && ry <= TY + 2 && rz >= 1 && rz <= TZ + 2) {
-      int r1 = ((rz - 1) * R1Y + (ry - 1)) * R1X + (rx - 1);
+    if (e < R1) {
 #pragma unroll
-      for (int v = 0; v < 8; ++v) s_c0[v * R1 + r1] = c[v];
+      for (int v = 0; v < 8; ++v) s_c0[v * R1 + e] = c[v];
     }
   }
   cp_async_wait_all();
