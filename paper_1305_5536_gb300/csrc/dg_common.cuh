@@ -126,7 +126,7 @@ __host__ __device__ constexpr int ring3d_count() {
   return TX * TY * TZ + 2 * (TY * TZ + TX * TZ + TX * TY);
 }
 template <int TX, int TY, int TZ>
-__device__ __forceinline__ void ring3d_cell(int e, int& rx, int& ry, int& rz) {
+__host__ __device__ __forceinline__ void ring3d_cell(int e, int& rx, int& ry, int& rz) {
   constexpr int NT = TX * TY * TZ, SX = TY * TZ, SY = TX * TZ, SZ = TX * TY;
   if (e < NT) {
     rx = e % TX + 1; ry = (e / TX) % TY + 1; rz = e / (TX * TY) + 1;
@@ -153,7 +153,7 @@ __host__ __device__ constexpr int halo3d_count() {
   return (TX + 2) * (TY + 2) * (TZ + 2) + 2 * (TY * TZ + TX * TZ + TX * TY);
 }
 template <int TX, int TY, int TZ>
-__device__ __forceinline__ void halo3d_cell(int e, int& rx, int& ry, int& rz) {
+__host__ __device__ __forceinline__ void halo3d_cell(int e, int& rx, int& ry, int& rz) {
   constexpr int R1X = TX + 2, R1Y = TY + 2, R1 = R1X * R1Y * (TZ + 2);
   constexpr int SX = TY * TZ, SY = TX * TZ, SZ = TX * TY;
   if (e < R1) {
@@ -177,13 +177,18 @@ __device__ __forceinline__ void halo3d_cell(int e, int& rx, int& ry, int& rz) {
 
 // Division of small non-negative integers by a divisor known only at run time (a
 // face count of a rolled loop over orientations): floor(n / d) = (n * m) >> 32
-// with m = ceil(2^32 / d), exact for n < 2^14 and d <= 1024 (checked for every
-// such pair); two instructions instead of a full integer division.
-__device__ __forceinline__ unsigned div_magic(unsigned d) {
+// with m = ceil(2^32 / d), exact for n < 2^14 and 2 <= d <= 1024 (checked for
+// every such pair; d = 1 would need m = 2^32); two instructions instead of a full
+// integer division.
+__host__ __device__ __forceinline__ unsigned div_magic(unsigned d) {
   return (unsigned)((0x100000000ull + d - 1) / d);
 }
-__device__ __forceinline__ int div_by_magic(int n, unsigned m) {
+__host__ __device__ __forceinline__ int div_by_magic(int n, unsigned m) {
+#ifdef __CUDA_ARCH__
   return (int)__umulhi((unsigned)n, m);
+#else
+  return (int)(((unsigned long long)(unsigned)n * m) >> 32);
+#endif
 }
 
 __host__ __device__ __forceinline__ int wrap_index(int g, int n) {
