@@ -13,7 +13,12 @@ step sooner) the solver restarts from the initial state, which stays resident on
 the device; the restart lies outside the timed events.  Kernel durations come from
 CUDA events the library records around each stage-kernel launch, in K more steps
 right after the timed ones (an event between the two stage kernels of a step
-serialises them; the timed steps let the second start while the first drains).  Multi-GPU
+serialises them; the timed steps let the second start while the first drains).
+End to end (``e2e``): every step the state goes in from page-locked host memory
+(dg_set_state), one step, and the state comes back into page-locked host memory
+(dg_get_state), with CUDA events; beside it the same loop in two contexts on two
+streams driven by two host threads at once (host clock), which shows how much the
+host link allows the transfers of one to overlap the other's.  Multi-GPU
 (--gpus N under torchrun): independent replicas, one per rank (weak scaling),
 barrier + max over ranks.  The default workload's line also carries the adjoint
 step time (the checkpointed adjoint of 100 steps of a 2D Euler 256^2 problem,
@@ -249,12 +254,15 @@ def run_gpu(args):
         loop through the C ABI with page-locked host buffers."""
         W = WORKLOADS[wname]
         u0, ncell, sizes = _workload_state(W)
-        if sizes is not None:
-            s = dg.DGSolver(configs=[dg.make_config(W["eq"], 2, (N, N), precision=prec)
-                                     for N in sizes])
-        else:
-            s = dg.DGSolver(W["eq"], W["dim"], W["n"], precision=prec, cfl=0.3,
-                            integrator=W.get("integrator", "rk2"))
+
+        def solver(stream=None):
+            if sizes is not None:
+                return dg.DGSolver(configs=[dg.make_config(W["eq"], 2, (N, N), precision=prec)
+                                            for N in sizes], stream=stream)
+            return dg.DGSolver(W["eq"], W["dim"], W["n"], precision=prec, cfl=0.3,
+                               integrator=W.get("integrator", "rk2"), stream=stream)
+
+        s = solver()
         u0_dev = torch.from_numpy(np.ascontiguousarray(u0)).to("cuda")
         cycle = W.get("restart", RESTART_STEPS)
         s.set_state(u0_dev)
@@ -328,8 +336,49 @@ def run_gpu(args):
                 s.get_state(host_out)
             e1.record(stream)
             barrier()
-            res["e2e_ms_per_step"] = e0.elapsed_time(e1) / e2e_K
+            res["e2e_ms_per_step"] = max_over_ranks(e0.elapsed_time(e1), "cuda") / e2e_K
             res["e2e_bytes"] = host_in.numel() * 8
+            # the same loop in two contexts, each on a stream of its own and driven by
+            # a host thread of its own (the library's calls release the GIL), so that
+            # one context's transfers and kernels may overlap the other's: what a
+            # caller stepping independent problems held in host memory gets
+            ctxs = []
+            for _ in range(2):
+                st_i = torch.cuda.Stream()
+                out_i = torch.empty_like(host_in).pin_memory()
+                s_i = solver(stream=st_i.cuda_stream)
+                s_i.set_state(host_in)
+                s_i.step(1)
+                s_i.get_state(out_i)
+                ctxs.append((s_i, out_i, st_i))
+            errors = []
+
+            def loop(i):
+                s_i, out_i, _ = ctxs[i]
+                try:
+                    for k in range(e2e_K):
+                        s_i.set_state(host_in)
+                        s_i.step(1)
+                        s_i.get_state(out_i)
+                except Exception as exc:  # re-raised on the main thread
+                    errors.append(exc)
+
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            threads = [threading.Thread(target=loop, args=(i,)) for i in range(2)]
+            for t in threads:
+                t.start()
+            for t in threads:
+                t.join()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter() - t0
+            barrier()
+            if errors:
+                raise errors[0]
+            res["e2e2_ms_per_step"] = max_over_ranks(t2, "cuda") * 1e3 / (2 * e2e_K)
+            for s_i, _, _ in ctxs:
+                s_i.close()
         s.close()
         return res
 
@@ -472,7 +521,15 @@ def run_gpu(args):
                     "launches": r32["kernel_launches"]},
         "fp64": fp64,
         "e2e": {"value": ws * ncell / (r32["e2e_ms_per_step"] * 1e-3), "unit": "cell-updates/s",
-                "h2d_bytes_per_step": r32["e2e_bytes"], "d2h_bytes_per_step": r32["e2e_bytes"]},
+                "h2d_bytes_per_step": r32["e2e_bytes"], "d2h_bytes_per_step": r32["e2e_bytes"],
+                "ms_per_step": r32["e2e_ms_per_step"],
+                "method": "dg_set_state from page-locked host memory, dg_step(1), dg_get_state "
+                          "into page-locked host memory, every step (CUDA events)",
+                "two_contexts": {
+                    "value": ws * ncell / (r32["e2e2_ms_per_step"] * 1e-3),
+                    "ms_per_step": r32["e2e2_ms_per_step"],
+                    "method": "the same loop in two contexts on two streams, driven by two host "
+                              "threads at once (host wall clock)"}},
         "gpu_launches": int(sum(r32["kernel_launches"])),
         "clocks": r32["clocks"],
     }

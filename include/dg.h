@@ -42,7 +42,9 @@
  * abort or trap; they return a dg_status and keep a per-context message
  * (dg_last_error).  Device-side problems (non-physical states, Riemann-solver
  * failure) set a sticky device word that the next synchronising call reports as
- * DG_ENONPHYS.  A context is not thread safe.
+ * DG_ENONPHYS.  A context is not thread safe: calls on one context must not
+ * overlap.  Different contexts may be driven from different host threads at the
+ * same time (the process-wide tile-shape tuning is serialised inside the library).
  */
 #ifndef DG_H
 #define DG_H

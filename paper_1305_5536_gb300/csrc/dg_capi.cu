@@ -11,6 +11,7 @@
 #include <cstddef>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -451,6 +452,9 @@ dg_status reset_ctl_and_cfl(dg_ctx* c) {
 // ---------------------------------------------------------------------------
 std::map<std::string, int> g_tune;
 bool g_tune_loaded = false;
+// contexts may be created and stepped from several host threads: one tuning at a
+// time (this also keeps concurrent trial steps from timing each other)
+std::mutex g_tune_mutex;
 
 std::string tune_key(dg_ctx* c) {
   char b[128];
@@ -502,6 +506,7 @@ dg_status autotune(dg_ctx* c) {
       return DG_OK;
     }
   }
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
   tune_load();
   std::string key = tune_key(c);
   auto it = g_tune.find(key);
