@@ -146,6 +146,47 @@ def test_adjoint_rollout_vs_central_differences_and_oracle():
     s.close()
 
 
+def test_adjoint_workload_full_size_vs_central_differences():
+    """The adjoint workload at its own size: 2D Euler 256^2, the seeded Gaussian
+    random density, 100 SSP-RK2 Courant steps at CFL 0.3 recorded with checkpoints
+    every 10, limiter off, FP64.  The checkpointed adjoint's directional derivative
+    <dJ/du_0, d> against central differences of the forward map with the recorded
+    time steps held fixed, 1e-6 relative (the forward map itself is held to the
+    oracle by the forward parity tests)."""
+    import torch
+    n, nsteps = (256, 256), 100
+    u0, _ = ics.euler2d_random_density(n)
+    target = ics.euler2d_random_density(n, seed=99)[0]
+    h = (1.0 / n[0], 1.0 / n[1])
+    # the Courant steps of the recording: the same state and rule, one at a time
+    c = dg.DGSolver("euler", 2, n, precision="fp64", limiter=0, cfl=0.3)
+    c.set_state(u0)
+    dts = []
+    for _ in range(nsteps):
+        dts.append(float(c.times()[1][0]))
+        c.step(1)
+    c.sync()
+    c.close()
+    s = dg.DGSolver("euler", 2, n, precision="fp64", limiter=0, cfl=0.3, ckpt_every=10)
+    s.set_state(u0)
+    s.record(nsteps)
+    uT = s.get_state()
+    np.testing.assert_allclose(_forward_fixed(n, u0, dts, "fp64", 0), uT, rtol=0,
+                               atol=1e-13 * np.abs(uT).max())
+    J0, gT = _objective_grad(uT, target, h)
+    g0 = s.adjoint(torch.from_numpy(gT).cuda()).cpu().numpy()
+    s.close()
+    rng = np.random.default_rng(23)
+    d = rng.standard_normal(u0.shape) * 1e-2
+    d[1:3] *= 10.0
+    gd = float((g0 * d).sum())
+    eps = 1e-5
+    Jp, _ = _objective_grad(_forward_fixed(n, u0 + eps * d, dts, "fp64", 0), target, h)
+    Jm, _ = _objective_grad(_forward_fixed(n, u0 - eps * d, dts, "fp64", 0), target, h)
+    fd = (Jp - Jm) / (2 * eps)
+    assert abs(gd - fd) < 1e-6 * abs(fd), (gd, fd)
+
+
 def test_autograd_rollout_fp32_gradient():
     import torch
     n = (32, 32)
