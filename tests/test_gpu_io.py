@@ -56,3 +56,20 @@ def test_state_transfer_paths_agree_batch():
     cfgs = [dg.make_config("mhd", 2, (N, N), precision="fp32") for N in sizes]
     u = np.concatenate([ics.orszag_tang((N, N)).ravel() for N in sizes])
     _three_ways(lambda: dg.DGSolver(configs=cfgs), u)
+
+
+def test_init_reports_enomem_when_the_state_does_not_fit():
+    """Maximum sizes: a configuration the check accepts (1.95e9 cells, under its
+    2e9 limit) whose state does not fit the device (3D MHD in FP64: three state
+    buffers of 484 GB each).  dg_init takes the first buffer (125 GB), fails on the
+    next with DG_ENOMEM and its message, frees what it took, and the device stays
+    usable for the next context."""
+    with pytest.raises(dg.DGError) as err:
+        dg.DGSolver("mhd", 3, (1250, 1250, 1250), precision="fp64")
+    assert err.value.status == dg.DG_ENOMEM
+    assert "allocation" in str(err.value)
+    n = (32, 32)
+    s = dg.DGSolver("euler", 2, n, precision="fp64")
+    s.set_state(ics.euler2d_wave(n))
+    s.step(2, sync=True)
+    s.close()
