@@ -1,7 +1,7 @@
 """Accuracy of the GPU paths over long runs, against the FP64 oracle.
 
-North star: the FP32 path's final-time L1 error and conservation drift are stated
-against the FP64 oracle.  Over many steps of a flow with shocks, the min/max
+The FP32 path's final-time L1 error and conservation drift, stated against the
+FP64 oracle.  Over many steps of a flow with shocks, the min/max
 limiter (a discontinuous function of its inputs, Sec. 2.5) amplifies any
 difference of rounding: two correct FP64 implementations drift apart.  The tests
 therefore also run the oracle on the initial state perturbed by 1e-14 relative
