@@ -1,4 +1,5 @@
-// dg_adjoint.cu -- reverse mode of the SSP-RK2 step of the 2D Euler DG scheme.
+// dg_adjoint.cu -- reverse mode of the SSP-RK2 step of the 2D DG scheme (Euler
+// with the min/max limiter or without; planar MHD without a limiter).
 //
 // Forward step with the time step dt held fixed (Lambda = limiter, L = DG
 // right-hand side):
@@ -355,6 +356,273 @@ __global__ void limit_vjp2d_kernel(StateBuf<TS> V, const double* __restrict__ nu
   }
 }
 
+// ---------------------------------------------------------------------------
+// Planar MHD (limiter off): out = a1 x1 + a2 x2 + beta J_L(U)^T y.  The face and
+// volume flux Jacobians are taken in forward mode: the scalar HLLD solver and
+// physical flux instantiated on dual numbers, one pass of six tangents per side
+// (the conserved point values rho, mx, my, E, Bx, By), contracted with the flux
+// adjoints.  Adjoint arrays in the interchange layout: planes v*3 + k of
+// (rho, mx, my, E), then b1, b2, a1, a2, a3 (12 .. 16).
+// ---------------------------------------------------------------------------
+template <class TC> struct VjpTileM;
+template <> struct VjpTileM<double> { static constexpr int X = 8, Y = 4; };
+template <> struct VjpTileM<float> { static constexpr int X = 8, Y = 8; };
+
+// The MHD branch of face_flux2d on dual conserved states.
+template <class TC, int N>
+__device__ void dface_flux2d_mhd(const Gas<Dn<TC, N>>& G, int dir, const Dn<TC, N>* cl,
+                                 const Dn<TC, N>* cr, Dn<TC, N>* F, unsigned& err) {
+  typedef Dn<TC, N> D;
+  const D rl = cl[0], rr = cr[0];
+  const D il = TC(1) / rl, ir = TC(1) / rr;
+  const D vxl = cl[1] * il, vyl = cl[2] * il, vxr = cr[1] * ir, vyr = cr[2] * ir;
+  const D magl = TC(0.5) * (cl[4] * cl[4] + cl[5] * cl[5]);
+  const D magr = TC(0.5) * (cr[4] * cr[4] + cr[5] * cr[5]);
+  const D pl = G.gm1 * (cl[3] - TC(0.5) * (cl[1] * vxl + cl[2] * vyl) - magl);
+  const D pr = G.gm1 * (cr[3] - TC(0.5) * (cr[1] * vxr + cr[2] * vyr) - magr);
+  const bool xd = dir == 0;
+  const D bn = TC(0.5) * (xd ? cl[4] + cr[4] : cl[5] + cr[5]);
+  D Ff[5];
+  hlld_flux<D>(G, rl, xd ? vxl : vyl, xd ? vyl : vxl, pl, xd ? cl[5] : cl[4], rr, xd ? vxr : vyr,
+               xd ? vyr : vxr, pr, xd ? cr[5] : cr[4], bn, Ff, err);
+  F[0] = Ff[0];
+  F[3] = Ff[3];
+  F[4] = Ff[4];
+  if (xd) { F[1] = Ff[1]; F[2] = Ff[2]; }
+  else { F[1] = Ff[2]; F[2] = Ff[1]; }
+}
+
+template <class TC>
+__device__ __forceinline__ void dual_gas(double gamma, Gas<Dn<TC, 6>>& G) {
+  G.set(gamma);
+}
+
+// Adjoints of both one-sided point states of one face Gauss point: lamL[i] =
+// sum_q mu[q] dF_q / dcl[i], lamR likewise.
+template <class TC>
+__device__ void face_flux2d_mhd_vjp(const Gas<Dn<TC, 6>>& GD, int dir, const TC* cl, const TC* cr,
+                                    const TC* mu, TC* lamL, TC* lamR, unsigned& err) {
+  typedef Dn<TC, 6> D;
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    D a[6], b[6], F[5];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      a[i] = D(cl[i]);
+      b[i] = D(cr[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) (side == 0 ? a : b)[i].d[i] = TC(1);
+    dface_flux2d_mhd<TC, 6>(GD, dir, a, b, F, err);
+    TC* lam = side == 0 ? lamL : lamR;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      TC t = TC(0);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) t += mu[q] * F[q].d[i];
+      lam[i] = t;
+    }
+  }
+}
+
+// Adjoint of the conserved point state of one volume Gauss point: a[i] =
+// sum_v (yx[v] dFx_v/dc_i + yy[v] dFy_v/dc_i).
+template <class TC>
+__device__ void phys_flux2d_mhd_vjp(const Gas<Dn<TC, 6>>& GD, const TC* c, const TC* yx,
+                                    const TC* yy, TC* a, unsigned& err) {
+  typedef Dn<TC, 6> D;
+  D cd[6], Fx[5], Fy[5];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    cd[i] = D(c[i]);
+    cd[i].d[i] = TC(1);
+  }
+  phys_flux2d<1, D>(GD, cd, Fx, Fy, err);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    TC t = TC(0);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) t += yx[v] * Fx[v].d[i] + yy[v] * Fy[v].d[i];
+    a[i] = t;
+  }
+}
+
+// Adjoint of the point values (rho, mx, my, E, Bx, By) at local point (x, y) of a
+// cell, added to the adjoints of its interchange coefficients (the transpose of
+// eval2d<1>: Bx = b1 + a3 x + a1 y, By = b2 + a2 x - a3 y).
+template <class TC>
+__device__ __forceinline__ void add_point_mhd(TC* acc, const TC* lam, TC x, TC y) {
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    acc[3 * v] += lam[v];
+    acc[3 * v + 1] += lam[v] * x;
+    acc[3 * v + 2] += lam[v] * y;
+  }
+  acc[12] += lam[4];
+  acc[13] += lam[5];
+  acc[14] += lam[4] * y;
+  acc[15] += lam[5] * x;
+  acc[16] += lam[4] * x - lam[5] * y;
+}
+
+template <class TC, class TS>
+__global__ void __launch_bounds__(VjpTileM<TC>::X * VjpTileM<TC>::Y)
+    rhs_vjp2d_mhd_kernel(StateBuf<TS> U, VjpArgs A) {
+  constexpr int AX = VjpTileM<TC>::X, AY = VjpTileM<TC>::Y, ANT = AX * AY;
+  constexpr int R1X = AX + 2, R1Y = AY + 2, R1 = R1X * R1Y;
+  constexpr int NFX = (AX + 1) * AY, NFY = AX * (AY + 1);
+  __shared__ TC s_c0[6 * R1], s_sl[11 * R1], s_y[17 * R1];
+  __shared__ TC s_lx[12 * 2 * NFX], s_ly[12 * 2 * NFY];
+  __shared__ int s_gx[R1X], s_gy[R1Y];
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * AX, j0 = blockIdx.y * AY;
+  const int nx = A.nx, ny = A.ny;
+  const size_t ncell = (size_t)A.ncell;
+  Gas<TC> G;
+  G.set(A.gamma);
+  Gas<Dn<TC, 6>> GD;
+  dual_gas<TC>(A.gamma, GD);
+  unsigned err = 0;
+  if (tid < R1X) s_gx[tid] = wrap_index(i0 - 1 + tid, nx);
+  else if (tid < R1X + R1Y) s_gy[tid - R1X] = wrap_index(j0 - 1 + (tid - R1X), ny) * nx;
+  __syncthreads();
+  for (int r = tid; r < R1; r += ANT) {
+    int ry = r / R1X, rx = r - ry * R1X;
+    size_t g = (size_t)s_gy[ry] + s_gx[rx];
+#pragma unroll
+    for (int v = 0; v < 6; ++v) s_c0[v * R1 + r] = Cvt<TC>::to_tc(U.c0[v * ncell + g]);
+#pragma unroll
+    for (int k = 0; k < 11; ++k) s_sl[k * R1 + r] = (TC)U.sl[k * ncell + g];
+#pragma unroll
+    for (int p = 0; p < 17; ++p) s_y[p * R1 + r] = Cvt<TC>::to_tc(A.y[p * ncell + g]);
+  }
+  __syncthreads();
+
+  const TC dx = (TC)A.dx, dy = (TC)A.dy;
+  const TC hx = TC(0.5) * dx, hy = TC(0.5) * dy;
+  const TC ox = dx * TC(0.28867513459481288225), oy = dy * TC(0.28867513459481288225);
+  const TC c3x = TC(3) / (dx * dx), c3y = TC(3) / (dy * dy);
+  const TC r3 = TC(1.7320508075688772935) / (dx * dy);
+  const TC ca3 = TC(1.7320508075688772935) / (dx * dx + dy * dy);
+  const TC i2x = TC(0.5) / dx, i2y = TC(0.5) / dy;
+  auto point = [&](int r, TC x, TC y, TC* c) {
+    TC c0[6], sl[11];
+#pragma unroll
+    for (int v = 0; v < 6; ++v) c0[v] = s_c0[v * R1 + r];
+#pragma unroll
+    for (int k = 0; k < 11; ++k) sl[k] = s_sl[k * R1 + r];
+    eval2d<1, TC>(c0, sl, x, y, c);
+  };
+
+  // ---- faces: adjoint of every Gauss-point flux -> adjoints of both states
+  for (int e = tid; e < 2 * (NFX + NFY); e += ANT) {
+    const bool xf = e < 2 * NFX;
+    const int ee = xf ? e : e - 2 * NFX;
+    const int f = ee >> 1, g = ee & 1;
+    const TC sg = g ? TC(1) : TC(-1);
+    int rl, rr;
+    TC xl, yl, xr, yr;
+    if (xf) {
+      int fy = f / (AX + 1), fx = f - fy * (AX + 1);
+      rl = (fy + 1) * R1X + fx;
+      rr = rl + 1;
+      xl = hx; xr = -hx; yl = yr = sg * oy;
+    } else {
+      int fy = f / AX, fx = f - fy * AX;
+      rl = fy * R1X + fx + 1;
+      rr = rl + R1X;
+      yl = hy; yr = -hy; xl = xr = sg * ox;
+    }
+    auto yL = [&](int p) { return s_y[p * R1 + rl]; };
+    auto yR = [&](int p) { return s_y[p * R1 + rr]; };
+    TC mu[5];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (xf)
+        mu[q] = (yR(3 * q) - yL(3 * q)) * i2x - c3x * (yL(3 * q + 1) + yR(3 * q + 1)) +
+                r3 * sg * (yR(3 * q + 2) - yL(3 * q + 2));
+      else
+        mu[q] = (yR(3 * q) - yL(3 * q)) * i2y - c3y * (yL(3 * q + 2) + yR(3 * q + 2)) +
+                r3 * sg * (yR(3 * q + 1) - yL(3 * q + 1));
+    }
+    // the transverse-field flux: b2, a2, a3 across x faces; b1, a1, a3 across y faces
+    if (xf)
+      mu[4] = (yR(13) - yL(13)) * i2x - c3x * (yL(15) + yR(15)) +
+              ca3 * (dy / dx) * sg * (yL(16) - yR(16));
+    else
+      mu[4] = (yR(12) - yL(12)) * i2y - c3y * (yL(14) + yR(14)) -
+              ca3 * (dx / dy) * sg * (yL(16) - yR(16));
+    TC cl[6], cr[6], lam[12];
+    point(rl, xl, yl, cl);
+    point(rr, xr, yr, cr);
+    face_flux2d_mhd_vjp<TC>(GD, xf ? 0 : 1, cl, cr, mu, lam, lam + 6, err);
+    if (xf) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) s_lx[(k * 2 + g) * NFX + f] = lam[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) s_ly[(k * 2 + g) * NFY + f] = lam[k];
+    }
+  }
+  __syncthreads();
+
+  // ---- per cell: gather faces and volume points
+  const int lx = tid % AX, ly = tid / AX;
+  const int gi = i0 + lx, gj = j0 + ly;
+  if (gi < nx && gj < ny) {
+    const int r = (ly + 1) * R1X + lx + 1;
+    TC acc[17];
+#pragma unroll
+    for (int p = 0; p < 17; ++p) acc[p] = TC(0);
+    const int fxm = ly * (AX + 1) + lx, fym = ly * AX + lx;
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const TC sg = g ? TC(1) : TC(-1);
+      TC l[6];
+      // x faces: this cell is the right state of face fxm, the left of fxm+1
+#pragma unroll
+      for (int v = 0; v < 6; ++v) l[v] = s_lx[((6 + v) * 2 + g) * NFX + fxm];
+      add_point_mhd<TC>(acc, l, -hx, sg * oy);
+#pragma unroll
+      for (int v = 0; v < 6; ++v) l[v] = s_lx[(v * 2 + g) * NFX + fxm + 1];
+      add_point_mhd<TC>(acc, l, hx, sg * oy);
+      // y faces: the upper state of fym, the lower state of fym+AX
+#pragma unroll
+      for (int v = 0; v < 6; ++v) l[v] = s_ly[((6 + v) * 2 + g) * NFY + fym];
+      add_point_mhd<TC>(acc, l, sg * ox, -hy);
+#pragma unroll
+      for (int v = 0; v < 6; ++v) l[v] = s_ly[(v * 2 + g) * NFY + fym + AX];
+      add_point_mhd<TC>(acc, l, sg * ox, hy);
+    }
+    // volume points: the x-flux sums enter the x slopes (and a2), the y-flux sums
+    // the y slopes (and a1), times 3/dx^2 and 3/dy^2
+    TC yx[5], yy[5];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      yx[q] = c3x * s_y[(3 * q + 1) * R1 + r];
+      yy[q] = c3y * s_y[(3 * q + 2) * R1 + r];
+    }
+    yx[4] = c3x * s_y[15 * R1 + r];
+    yy[4] = c3y * s_y[14 * R1 + r];
+#pragma unroll 1
+    for (int qp = 0; qp < 4; ++qp) {
+      const TC xq = (qp & 1) ? ox : -ox, yq = (qp & 2) ? oy : -oy;
+      TC c[6], a[6];
+      point(r, xq, yq, c);
+      phys_flux2d_mhd_vjp<TC>(GD, c, yx, yy, a, err);
+      add_point_mhd<TC>(acc, a, xq, yq);
+    }
+    const size_t gc = (size_t)gj * nx + gi;
+#pragma unroll
+    for (int p = 0; p < 17; ++p) {
+      double o = A.a1 * A.x1[p * ncell + gc] + A.beta * Cvt<TC>::to_f64(acc[p]);
+      if (A.x2) o += A.a2 * A.x2[p * ncell + gc];
+      A.out[p * ncell + gc] = o;
+    }
+  }
+  if (err) atomicOr(A.err, err);
+}
+
 __global__ void axpby_kernel(const double* __restrict__ a, double sa, const double* __restrict__ b,
                              double sb, double* __restrict__ o, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
@@ -397,6 +665,7 @@ StateBuf<TS> sb(const Work& w, int k) {
 size_t carve_into(char* base, const AdjointCall& c, int seg, Work* w) {
   const size_t n = (size_t)c.nx * c.ny;
   const size_t ts = c.fp32 ? 4 : 8;
+  const size_t nv = c.eq ? 6 : 4, ns = c.eq ? 11 : 8, np = c.eq ? 17 : 12;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     char* r = base ? base + off : nullptr;
@@ -408,15 +677,15 @@ size_t carve_into(char* base, const AdjointCall& c, int seg, Work* w) {
   t.fp32 = c.fp32;
   t.seg = seg;
   for (int k = 0; k < 4; ++k) {
-    t.c0[k] = (double*)take(n * 4 * 8);
-    t.sl[k] = take(n * 8 * ts);
+    t.c0[k] = (double*)take(n * nv * 8);
+    t.sl[k] = take(n * ns * ts);
   }
-  for (int k = 0; k < 3; ++k) t.lam[k] = (double*)take(n * 12 * 8);
-  t.lamrun[0] = (double*)take(n * 12 * 8);
-  t.lamrun[1] = (double*)take(n * 12 * 8);
+  for (int k = 0; k < 3; ++k) t.lam[k] = (double*)take(n * np * 8);
+  t.lamrun[0] = (double*)take(n * np * 8);
+  t.lamrun[1] = (double*)take(n * np * 8);
   t.ctl = (Ctl*)take(sizeof(Ctl));
   t.err = (unsigned*)take(sizeof(unsigned));
-  t.segbuf = (double*)take((size_t)seg * n * 12 * 8);
+  t.segbuf = (double*)take((size_t)seg * n * np * 8);
   if (w) *w = t;
   return off;
 }
@@ -444,27 +713,36 @@ bool carve(const AdjointStore& S, const AdjointCall& c, int seg, Work* w) {
   return carve_into((char*)S.work, c, seg, w) <= S.work_bytes;
 }
 
-// The 12 interchange planes of a 2D Euler state: plane v*3 + k is average v (k = 0)
-// or derivative coefficient v*2 + k - 1.  Converted in one launch per state.
-PlaneMap euler2d_planes() {
+// The interchange planes of a 2D state: plane v*3 + k is average v (k = 0) or
+// derivative coefficient v*2 + k - 1 of (rho, mx, my, E); planar MHD adds b1, b2
+// (averages 4, 5) and a1, a2, a3 (coefficients 8, 9, 10).  Converted in one
+// launch per state.
+PlaneMap planes2d(int eq) {
   PlaneMap m{};
-  m.nplanes = 12;
+  m.nplanes = eq ? 17 : 12;
   for (int p = 0; p < 12; ++p) {
     const int v = p / 3, k = p % 3;
     m.kind[p] = k == 0 ? 0 : 1;
     m.idx[p] = k == 0 ? v : v * 2 + (k - 1);
   }
+  if (eq) {
+    const int kind[5] = {0, 0, 1, 1, 1}, idx[5] = {4, 5, 8, 9, 10};
+    for (int q = 0; q < 5; ++q) {
+      m.kind[12 + q] = kind[q];
+      m.idx[12 + q] = idx[q];
+    }
+  }
   return m;
 }
 
 template <class TS>
-cudaError_t to_internal(const double* src, StateBuf<TS> dst, long n, cudaStream_t st) {
-  return launch_state_in<TS>(src, dst, euler2d_planes(), n, st);
+cudaError_t to_internal(int eq, const double* src, StateBuf<TS> dst, long n, cudaStream_t st) {
+  return launch_state_in<TS>(src, dst, planes2d(eq), n, st);
 }
 
 template <class TS>
-cudaError_t to_interchange(StateBuf<TS> src, double* dst, long n, cudaStream_t st) {
-  return launch_state_out<TS>(src, dst, euler2d_planes(), n, st);
+cudaError_t to_interchange(int eq, StateBuf<TS> src, double* dst, long n, cudaStream_t st) {
+  return launch_state_out<TS>(src, dst, planes2d(eq), n, st);
 }
 
 template <class TS>
@@ -490,6 +768,12 @@ cudaError_t apply_rhs_vjp(const AdjointCall& c, const Work& w, StateBuf<TS> U, c
   A.dx = c.dx; A.dy = c.dy; A.gamma = c.gamma;
   A.y = y; A.x1 = x1; A.a1 = a1; A.x2 = x2; A.a2 = a2; A.beta = beta; A.out = out;
   A.err = w.err;
+  if (c.eq) {
+    constexpr int AX = VjpTileM<TC>::X, AY = VjpTileM<TC>::Y;
+    dim3 grid((c.nx + AX - 1) / AX, (c.ny + AY - 1) / AY);
+    rhs_vjp2d_mhd_kernel<TC, TS><<<grid, AX * AY, 0, c.stream>>>(U, A);
+    return cudaGetLastError();
+  }
   constexpr int AX = VjpTile<TC>::X, AY = VjpTile<TC>::Y;
   dim3 grid((c.nx + AX - 1) / AX, (c.ny + AY - 1) / AY);
   rhs_vjp2d_kernel<TC, TS><<<grid, AX * AY, 0, c.stream>>>(U, A);
@@ -503,8 +787,9 @@ cudaError_t reverse_step(const AdjointCall& c, const Work& w, const double* lam_
   const long n = (long)c.nx * c.ny;
   StateBuf<TS> Vn = sb<TS>(w, 0), Un = sb<TS>(w, 1), V1 = sb<TS>(w, 2), U1 = sb<TS>(w, 3);
   cudaError_t e;
+  if (c.eq && c.limiter) return cudaErrorNotSupported;  // the limiter's transpose is Euler's
   // forward recompute of the stage states
-  e = launch_stage2d(0, 0, 1, stage_args<TS>(c, w, Vn, Vn, V1, dt), c.stream);
+  e = launch_stage2d(c.eq, 0, 1, stage_args<TS>(c, w, Vn, Vn, V1, dt), c.stream);
   if (e != cudaSuccess) return e;
   if (c.limiter) {
     limit2d_kernel<TC, TS><<<grid1d(n), 256, 0, c.stream>>>(Vn, Un, c.nx, c.ny, c.dx, c.dy, c.gamma);
@@ -573,7 +858,7 @@ dg_status step_t(AdjointStore& S, const AdjointCall& c, const double* u_n, const
   cudaError_t e;
   if ((e = cudaMemsetAsync(w.err, 0, sizeof(unsigned), c.stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), c.stream)) != cudaSuccess ||
-      (e = to_internal<TS>(u_n, sb<TS>(w, 0), n, c.stream)) != cudaSuccess ||
+      (e = to_internal<TS>(c.eq, u_n, sb<TS>(w, 0), n, c.stream)) != cudaSuccess ||
       (e = reverse_step<TC, TS>(c, w, lam_next, lam_prev, dt)) != cudaSuccess) {
     msg = std::string("adjoint step: ") + cudaGetErrorString(e);
     return DG_ECUDA;
@@ -592,7 +877,7 @@ dg_status run_t(AdjointStore& S, const AdjointCall& c, int k, const double* lam_
     return DG_ESTATE;
   }
   const long n = (long)c.nx * c.ny;
-  const size_t plane = (size_t)n * 12;
+  const size_t plane = (size_t)n * (c.eq ? 17 : 12);
   std::vector<double> dts((size_t)S.nrec);
   cudaError_t e = cudaMemcpyAsync(dts.data(), S.dt_hist, S.nrec * sizeof(double),
                                   cudaMemcpyDeviceToHost, c.stream);
@@ -617,17 +902,17 @@ dg_status run_t(AdjointStore& S, const AdjointCall& c, int k, const double* lam_
     if ((e = cudaMemcpyAsync(w.segbuf, ck, plane * 8, cudaMemcpyDeviceToDevice, c.stream)) !=
         cudaSuccess)
       break;
-    if ((e = to_internal<TS>(ck, sb<TS>(w, 0), n, c.stream)) != cudaSuccess) break;
+    if ((e = to_internal<TS>(c.eq, ck, sb<TS>(w, 0), n, c.stream)) != cudaSuccess) break;
     int a = 0;  // buffers 0 and 1 take turns as the step's input and output
     for (long long m = n0; m + 1 < n1; ++m) {
       const double dt = dts[(size_t)m];
-      if ((e = launch_stage2d(0, 0, 1, stage_args<TS>(c, w, sb<TS>(w, a), sb<TS>(w, a), sb<TS>(w, 2), dt),
+      if ((e = launch_stage2d(c.eq, 0, 1, stage_args<TS>(c, w, sb<TS>(w, a), sb<TS>(w, a), sb<TS>(w, 2), dt),
                               c.stream)) != cudaSuccess)
         break;
-      if ((e = launch_stage2d(0, 0, 2, stage_args<TS>(c, w, sb<TS>(w, 2), sb<TS>(w, a), sb<TS>(w, 1 - a), dt),
+      if ((e = launch_stage2d(c.eq, 0, 2, stage_args<TS>(c, w, sb<TS>(w, 2), sb<TS>(w, a), sb<TS>(w, 1 - a), dt),
                               c.stream)) != cudaSuccess)
         break;
-      if ((e = to_interchange<TS>(sb<TS>(w, 1 - a), w.segbuf + (size_t)(m + 1 - n0) * plane, n,
+      if ((e = to_interchange<TS>(c.eq, sb<TS>(w, 1 - a), w.segbuf + (size_t)(m + 1 - n0) * plane, n,
                                   c.stream)) != cudaSuccess)
         break;
       a = 1 - a;
@@ -635,7 +920,7 @@ dg_status run_t(AdjointStore& S, const AdjointCall& c, int k, const double* lam_
     if (e != cudaSuccess) break;
     // reverse through the segment
     for (long long m = n1 - 1; m >= n0; --m) {
-      if ((e = to_internal<TS>(w.segbuf + (size_t)(m - n0) * plane, sb<TS>(w, 0), n, c.stream)) !=
+      if ((e = to_internal<TS>(c.eq, w.segbuf + (size_t)(m - n0) * plane, sb<TS>(w, 0), n, c.stream)) !=
           cudaSuccess)
         break;
       double* dst = (m == 0) ? lam_0 : w.lamrun[cur ^ 1];

@@ -1,5 +1,5 @@
 // dg_adjoint.h -- reverse-mode (vector-Jacobian) products of the SSP-RK2 step of
-// the 2D Euler DG scheme, and the checkpoint store used to run them backwards
+// the 2D DG scheme, and the checkpoint store used to run them backwards
 // over a recorded trajectory.
 #pragma once
 
@@ -29,6 +29,7 @@ struct AdjointStore {
 };
 
 struct AdjointCall {
+  int eq;  // DG_EULER or DG_MHD
   int nx, ny;
   double dx, dy, gamma;
   int limiter, fp32;

@@ -983,13 +983,16 @@ dg_status dg_adjoint_step(dg_ctx* c, const double* lam_next, double* lam_prev, c
   if (c->integrator != DG_SSPRK2) return fail(c, DG_EINVAL, "the adjoint is that of the SSP-RK2 step");
   if (c->limiter == 2)
     return fail(c, DG_EINVAL, "the adjoint covers the min/max limiter (limiter 0 or 1)");
-  if (c->eq != DG_EULER || c->dim != 2 || c->probs.size() != 1)
-    return fail(c, DG_EINVAL, "the adjoint is implemented for one 2D Euler problem");
+  if (c->dim != 2 || c->probs.size() != 1)
+    return fail(c, DG_EINVAL, "the adjoint is implemented for one 2D problem");
+  if (c->eq == DG_MHD && c->limiter != 0)
+    return fail(c, DG_EINVAL, "the planar MHD adjoint is that of the step without a limiter");
   if (!(dt > 0.0)) return fail(c, DG_EINVAL, "dt must be > 0");
   AdjointCall call;
   call.nx = c->probs[0].nx; call.ny = c->probs[0].ny;
   call.dx = c->probs[0].dx; call.dy = c->probs[0].dy;
   call.gamma = c->gamma; call.limiter = c->limiter; call.fp32 = c->fp32;
+  call.eq = c->eq;
   call.stream = c->stream;
   std::string msg;
   dg_status s = adjoint_step(c->adj, call, u_n, lam_next, lam_prev, dt, msg);
@@ -1004,8 +1007,10 @@ dg_status dg_record(dg_ctx* c, int nsteps, double dt_override, double* t_out) {
   if (c->integrator != DG_SSPRK2) return fail(c, DG_EINVAL, "the adjoint is that of the SSP-RK2 step");
   if (c->limiter == 2)
     return fail(c, DG_EINVAL, "the adjoint covers the min/max limiter (limiter 0 or 1)");
-  if (c->eq != DG_EULER || c->dim != 2 || c->probs.size() != 1)
-    return fail(c, DG_EINVAL, "the adjoint is implemented for one 2D Euler problem");
+  if (c->dim != 2 || c->probs.size() != 1)
+    return fail(c, DG_EINVAL, "the adjoint is implemented for one 2D problem");
+  if (c->eq == DG_MHD && c->limiter != 0)
+    return fail(c, DG_EINVAL, "the planar MHD adjoint is that of the step without a limiter");
   if (nsteps < 0) return fail(c, DG_EINVAL, "nsteps must be >= 0");
   const Prob& p = c->probs[0];
   std::string msg;
@@ -1067,6 +1072,7 @@ dg_status dg_adjoint(dg_ctx* c, const double* lam_N, double* lam_0) {
   AdjointCall call;
   call.nx = p.nx; call.ny = p.ny; call.dx = p.dx; call.dy = p.dy;
   call.gamma = c->gamma; call.limiter = c->limiter; call.fp32 = c->fp32;
+  call.eq = c->eq;
   call.stream = c->stream;
   std::string msg;
   dg_status s = adjoint_run(c->adj, call, c->nplanes, c->ckpt_every, lam_N, lam_0, msg);

@@ -13,6 +13,13 @@ template <class T, int N>
 struct Dn {
   T v;
   T d[N];
+  Dn() = default;
+  // a constant (zero tangents), so that code written for a scalar type T (its
+  // T(0.5), T(1) ...) also runs on Dn<T, N>
+  __host__ __device__ Dn(T a) : v(a) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) d[i] = T(0);
+  }
 };
 
 template <class T, int N>
@@ -125,6 +132,29 @@ __device__ __forceinline__ Dn<T, N> dpow(const Dn<T, N>& a, T e) {
 }
 template <class T, int N>
 __device__ __forceinline__ Dn<T, N> dabs(const Dn<T, N>& a) { return a.v < T(0) ? -a : a; }
+
+// What the scalar device physics needs besides arithmetic, so that its templates
+// (hlld_flux, fast_speed, phys_flux2d) instantiate on Dn<T, N>: comparisons of
+// the values (branches follow the value: the derivative of the active branch),
+// |x|, the square root, and the solver tolerances of the scalar type.
+template <class T, int N>
+__device__ __forceinline__ bool operator<(const Dn<T, N>& a, const Dn<T, N>& b) { return a.v < b.v; }
+template <class T, int N>
+__device__ __forceinline__ bool operator>(const Dn<T, N>& a, const Dn<T, N>& b) { return a.v > b.v; }
+template <class T, int N>
+__device__ __forceinline__ bool operator<=(const Dn<T, N>& a, const Dn<T, N>& b) { return a.v <= b.v; }
+template <class T, int N>
+__device__ __forceinline__ bool operator>=(const Dn<T, N>& a, const Dn<T, N>& b) { return a.v >= b.v; }
+template <class T, int N>
+__device__ __forceinline__ Dn<T, N> fabs(const Dn<T, N>& a) { return dabs(a); }
+template <class T, int N>
+__device__ __forceinline__ Dn<T, N> rsqrtv(const Dn<T, N>& a) { return dsqrt(a); }
+template <class T, int N>
+struct Prec<Dn<T, N>> {
+  static constexpr T newton_tol = Prec<T>::newton_tol;
+  static constexpr int newton_max = Prec<T>::newton_max;
+  static constexpr T hlld_degenerate = Prec<T>::hlld_degenerate;
+};
 
 // Primitive (rho, u, v, p) of conserved (rho, mx, my, E) in 2D, dual.
 template <class T, int N>

@@ -1,4 +1,5 @@
-"""Adjoint (vector-Jacobian products) of the 2D Euler DG step on the GPU.
+"""Adjoint (vector-Jacobian products) of the 2D Euler and planar MHD DG steps on
+the GPU.
 
 Checked against the oracle's FP64 tangent model (dot-product identity
 <J^T lam, d> = <lam, J d>), against the full Jacobian built column by column
@@ -281,3 +282,124 @@ def test_fp32_limited_adjoint_agrees_with_fp64_away_from_branch_flips(n, capsys)
               "max %.2e" % (n, frac_ok, float(np.median(cell_err)), float(cell_err.max())))
     assert frac_ok >= 0.95, frac_ok
     assert float(np.median(cell_err)) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Planar MHD without a limiter: the face and volume flux Jacobians (HLLD and
+# the physical flux, with the divergence-free field basis) in the transposed
+# right-hand side.
+# ---------------------------------------------------------------------------
+def _mhd_state(n):
+    u = ics.orszag_tang(n)
+    return ics.add_slope_noise(u, 0, 2, 0.05, np.random.default_rng(5))
+
+
+def _vjp_mhd(n, u, lam, dt, prec, box=(1.0, 0.9)):
+    import torch
+    s = dg.DGSolver("mhd", 2, n, box=box + (1.0,), precision=prec, limiter=0)
+    out = s.adjoint_step(torch.from_numpy(lam).cuda(), torch.from_numpy(u).cuda(), dt)
+    torch.cuda.synchronize()
+    s.close()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+@pytest.mark.parametrize("n", [(12, 10), (37, 29), (5, 3)])
+def test_mhd_adjoint_step_dot_product(prec, tol, n):
+    """<J^T lam, d> from the GPU against <lam, J d> from the oracle's FP64 tangent
+    of the planar MHD step (limiter off), every plane of lam and d random."""
+    u = _mhd_state(n)
+    P = O.Problem(O.MHD, 2, n, box=(1.0, 0.9), limiter=0)
+    dt = 0.5 * P.cfl_dt(u)[0]
+    rng = np.random.default_rng(11)
+    lam = rng.standard_normal(u.shape)
+    d = rng.standard_normal(u.shape)
+    _, Jd, fl = P.tangent_step(u, d, dt)
+    assert fl == 0
+    JTl = _vjp_mhd(n, u, lam, dt, prec)
+    a, b = float((JTl * d).sum()), float((lam * Jd).sum())
+    scale = float(np.abs(JTl * d).sum())
+    assert abs(a - b) < tol * scale, (a, b)
+
+
+def test_mhd_adjoint_full_jacobian_tiny():
+    """Every column of the planar MHD step's Jacobian on a 4 x 3 grid: J^T e_i
+    from the GPU against the oracle's tangent J e_j, entry by entry."""
+    n = (4, 3)
+    u = _mhd_state(n)
+    P = O.Problem(O.MHD, 2, n, box=(1.0, 0.9), limiter=0)
+    dt = 0.5 * P.cfl_dt(u)[0]
+    m = u.size
+    J = np.zeros((m, m))
+    for j in range(m):
+        e = np.zeros(m)
+        e[j] = 1.0
+        _, col, fl = P.tangent_step(u, e.reshape(u.shape), dt)
+        assert fl == 0
+        J[:, j] = col.ravel()
+    rng = np.random.default_rng(13)
+    for _ in range(3):
+        lam = rng.standard_normal(u.shape)
+        JTl = _vjp_mhd(n, u, lam, dt, "fp64")
+        np.testing.assert_allclose(JTl.ravel(), J.T @ lam.ravel(), rtol=0,
+                                   atol=1e-12 * np.abs(J.T @ lam.ravel()).max())
+
+
+def _forward_fixed_eq(eq, n, u0, dts, prec, limiter):
+    s = dg.DGSolver(eq, 2, n, precision=prec, limiter=limiter)
+    s.set_state(u0)
+    for dt in dts:
+        s.step(1, dt=dt)
+    s.sync()
+    out = s.get_state()
+    s.close()
+    return out
+
+
+def test_mhd_adjoint_rollout_vs_central_differences():
+    """A checkpointed planar MHD rollout (24 x 20, 8 Courant steps, checkpoints
+    every 3, limiter off), FP64: the adjoint's directional derivative of the
+    density misfit against central differences of the forward map with the
+    recorded time steps, 1e-6."""
+    import torch
+    n, nsteps = (24, 20), 8
+    u0 = _mhd_state(n)
+    h = (1.0 / n[0], 1.0 / n[1])
+    c = dg.DGSolver("mhd", 2, n, precision="fp64", limiter=0)
+    c.set_state(u0)
+    dts = []
+    for _ in range(nsteps):
+        dts.append(float(c.times()[1][0]))
+        c.step(1)
+    c.sync()
+    c.close()
+    s = dg.DGSolver("mhd", 2, n, precision="fp64", limiter=0, ckpt_every=3)
+    s.set_state(u0)
+    s.record(nsteps)
+    uT = s.get_state()
+    np.testing.assert_allclose(_forward_fixed_eq("mhd", n, u0, dts, "fp64", 0), uT, rtol=0,
+                               atol=1e-13 * np.abs(uT).max())
+    target = ics.orszag_tang(n)
+    target[0] *= 1.1
+    J0, gT = _objective_grad(uT, target, h)
+    g0 = s.adjoint(torch.from_numpy(gT).cuda()).cpu().numpy()
+    s.close()
+    rng = np.random.default_rng(29)
+    d = rng.standard_normal(u0.shape) * 1e-2
+    eps = 1e-5
+    Jp, _ = _objective_grad(_forward_fixed_eq("mhd", n, u0 + eps * d, dts, "fp64", 0), target, h)
+    Jm, _ = _objective_grad(_forward_fixed_eq("mhd", n, u0 - eps * d, dts, "fp64", 0), target, h)
+    fd = (Jp - Jm) / (2 * eps)
+    gd = float((g0 * d).sum())
+    assert abs(gd - fd) < 1e-6 * abs(fd), (gd, fd)
+
+
+def test_mhd_adjoint_with_limiter_is_refused():
+    import torch
+    n = (8, 8)
+    s = dg.DGSolver("mhd", 2, n, precision="fp64", limiter=1)
+    u = torch.from_numpy(_mhd_state(n)).cuda()
+    with pytest.raises(dg.DGError) as err:
+        s.adjoint_step(u.clone(), u, 1e-3)
+    assert err.value.status == dg.DG_EINVAL
+    s.close()
