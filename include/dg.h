@@ -164,11 +164,9 @@ dg_status dg_divb(dg_ctx* ctx, double* out, int on_device);
  * DG_SSPRK2 contexts only):
  *   lam_prev = (d U^{n+1} / d U^n)^T lam_next,   U^{n+1} = step(U^n; dt).
  * u_n, lam_next, lam_prev: device pointers, interchange layout, float64; lam_prev
- * may not alias the other two.  One 2D problem: Euler with limiter 0 or 1 (the
- * limiter contributes the derivative of its active branch), or planar MHD with
- * limiter 0 (the face and volume flux Jacobians of HLLD and of the physical
- * flux, the divergence-free field basis included).  Other configurations:
- * DG_EINVAL.  The context's own state is not changed.  Enqueued on the context
+ * may not alias the other two.  One 2D problem, Euler or planar MHD (HLLD, the
+ * divergence-free field basis), limiter 0 or 1 (the limiter contributes the
+ * derivative of its active branch).  Other configurations: DG_EINVAL.  The context's own state is not changed.  Enqueued on the context
  * stream. */
 dg_status dg_adjoint_step(dg_ctx* ctx, const double* lam_next, double* lam_prev,
                           const double* u_n, double dt);

@@ -1,5 +1,5 @@
 // dg_adjoint.cu -- reverse mode of the SSP-RK2 step of the 2D DG scheme (Euler
-// with the min/max limiter or without; planar MHD without a limiter).
+// and planar MHD, with the min/max limiter or without).
 //
 // Forward step with the time step dt held fixed (Lambda = limiter, L = DG
 // right-hand side):
@@ -623,6 +623,126 @@ __global__ void __launch_bounds__(VjpTileM<TC>::X * VjpTileM<TC>::Y)
   if (err) atomicOr(A.err, err);
 }
 
+// Interchange planes of the internal averages (rho, mx, my, E, b1, b2) and
+// derivative coefficients (x and y slopes of the four Taylor variables, a1, a2,
+// a3) of a planar MHD state.
+__device__ __forceinline__ int mhd_avg_plane(int v) { return v < 4 ? 3 * v : 8 + v; }
+__device__ __forceinline__ int mhd_slope_plane(int k) { return k < 8 ? 3 * (k >> 1) + 1 + (k & 1) : 6 + k; }
+
+// U = Lambda(V) for planar MHD (internal layout): the forward limiter of the
+// stage kernels, cell by cell from global memory.
+template <class TC, class TS>
+__global__ void limit2d_mhd_kernel(StateBuf<TS> V, StateBuf<TS> U, int nx, int ny, double dx,
+                                   double dy, double gamma) {
+  const long ncell = (long)nx * ny;
+  Gas<TC> G;
+  G.set(gamma);
+  const TC hh[2] = {TC(0.5 * dx), TC(0.5 * dy)};
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx), j = (int)(c / nx);
+    const long nb[4] = {(long)j * nx + wrap_index(i - 1, nx), (long)j * nx + wrap_index(i + 1, nx),
+                        (long)wrap_index(j - 1, ny) * nx + i, (long)wrap_index(j + 1, ny) * nx + i};
+    TC cc[6], W[6], Wn[4][6], s[11];
+    unsigned err = 0;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) cc[v] = Cvt<TC>::to_tc(V.c0[v * ncell + c]);
+    prims2d<1, TC>(G, cc, W, err);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      TC cn[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) cn[v] = Cvt<TC>::to_tc(V.c0[v * ncell + nb[k]]);
+      prims2d<1, TC>(G, cn, Wn[k], err);
+    }
+#pragma unroll
+    for (int k = 0; k < 11; ++k) s[k] = (TC)V.sl[k * ncell + c];
+    limit_cell2d<1, TC>(G, hh, W, Wn, s);
+#pragma unroll
+    for (int v = 0; v < 6; ++v) U.c0[v * ncell + c] = V.c0[v * ncell + c];
+#pragma unroll
+    for (int k = 0; k < 11; ++k) U.sl[k * ncell + c] = (TS)s[k];
+  }
+}
+
+// out = J_Lambda(V)^T nu for planar MHD (interchange layout): the forward limiter
+// instantiated on dual numbers, six tangents a pass.  A cell's limited slopes
+// depend on its own averages and slopes (three passes) and on its four
+// neighbours' averages; its averages also enter its neighbours' limiters (one pass
+// each).  Branches follow the values (the active branch's derivative).
+template <class TC, class TS>
+__global__ void limit_vjp2d_mhd_kernel(StateBuf<TS> V, const double* __restrict__ nu, double* out,
+                                       int nx, int ny, double dx, double dy, double gamma) {
+  typedef Dn<TC, 6> D;
+  const long ncell = (long)nx * ny;
+  Gas<D> GD;
+  GD.set(gamma);
+  const D hh[2] = {D(TC(0.5 * dx)), D(TC(0.5 * dy))};
+  const int ofs[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx), j = (int)(c / nx);
+    auto at = [&](int di, int dj) {
+      return (long)wrap_index(j + dj, ny) * nx + wrap_index(i + di, nx);
+    };
+    unsigned err = 0;
+    // the limiter of cell e with tangents seeded by `seed` (which inputs, in
+    // which order), contracted with e's slope adjoints: a[t] for t < nt
+    auto pass = [&](long e, int ei, int ej, int kind, int first, int nt, TC* a) {
+      D c0[6], s[11], cn[4][6], W[6], Wn[4][6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) c0[v] = D(Cvt<TC>::to_tc(V.c0[v * ncell + e]));
+#pragma unroll
+      for (int k = 0; k < 11; ++k) s[k] = D((TC)V.sl[k * ncell + e]);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const long q = at(ei + ofs[m][0], ej + ofs[m][1]);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) cn[m][v] = D(Cvt<TC>::to_tc(V.c0[v * ncell + q]));
+      }
+      for (int t = 0; t < nt; ++t) {
+        if (kind == 0) c0[first + t].d[t] = TC(1);       // own averages
+        else if (kind == 1) s[first + t].d[t] = TC(1);   // own slopes
+        else cn[kind - 2][first + t].d[t] = TC(1);       // neighbour kind-2's averages
+      }
+      prims2d<1, D>(GD, c0, W, err);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) prims2d<1, D>(GD, cn[m], Wn[m], err);
+      limit_cell2d<1, D>(GD, hh, W, Wn, s);
+      for (int t = 0; t < nt; ++t) {
+        TC x = TC(0);
+#pragma unroll
+        for (int k = 0; k < 11; ++k)
+          x += Cvt<TC>::to_tc(nu[mhd_slope_plane(k) * ncell + e]) * s[k].d[t];
+        a[t] = x;
+      }
+    };
+    TC acc[17];
+#pragma unroll
+    for (int p = 0; p < 17; ++p) acc[p] = TC(0);
+    // the averages pass through the limiter unchanged
+#pragma unroll
+    for (int v = 0; v < 6; ++v) acc[mhd_avg_plane(v)] = Cvt<TC>::to_tc(nu[mhd_avg_plane(v) * ncell + c]);
+    TC a[6];
+    // (a) this cell's own limiter: its averages, then its slopes in two passes
+    pass(c, 0, 0, 0, 0, 6, a);
+    for (int t = 0; t < 6; ++t) acc[mhd_avg_plane(t)] += a[t];
+    pass(c, 0, 0, 1, 0, 6, a);
+    for (int t = 0; t < 6; ++t) acc[mhd_slope_plane(t)] += a[t];
+    pass(c, 0, 0, 1, 6, 5, a);
+    for (int t = 0; t < 5; ++t) acc[mhd_slope_plane(6 + t)] += a[t];
+    // (b) each neighbour e's limiter reads this cell's averages as its
+    //     neighbour number k ^ 1 (left <-> right, down <-> up)
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+      pass(at(ofs[k][0], ofs[k][1]), ofs[k][0], ofs[k][1], 2 + (k ^ 1), 0, 6, a);
+      for (int t = 0; t < 6; ++t) acc[mhd_avg_plane(t)] += a[t];
+    }
+#pragma unroll
+    for (int p = 0; p < 17; ++p) out[p * ncell + c] = Cvt<TC>::to_f64(acc[p]);
+  }
+}
+
 __global__ void axpby_kernel(const double* __restrict__ a, double sa, const double* __restrict__ b,
                              double sb, double* __restrict__ o, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
@@ -787,11 +907,14 @@ cudaError_t reverse_step(const AdjointCall& c, const Work& w, const double* lam_
   const long n = (long)c.nx * c.ny;
   StateBuf<TS> Vn = sb<TS>(w, 0), Un = sb<TS>(w, 1), V1 = sb<TS>(w, 2), U1 = sb<TS>(w, 3);
   cudaError_t e;
-  if (c.eq && c.limiter) return cudaErrorNotSupported;  // the limiter's transpose is Euler's
   // forward recompute of the stage states
   e = launch_stage2d(c.eq, 0, 1, stage_args<TS>(c, w, Vn, Vn, V1, dt), c.stream);
   if (e != cudaSuccess) return e;
-  if (c.limiter) {
+  if (c.limiter && c.eq) {
+    limit2d_mhd_kernel<TC, TS><<<grid1d(n), 256, 0, c.stream>>>(Vn, Un, c.nx, c.ny, c.dx, c.dy, c.gamma);
+    limit2d_mhd_kernel<TC, TS><<<grid1d(n), 256, 0, c.stream>>>(V1, U1, c.nx, c.ny, c.dx, c.dy, c.gamma);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if (c.limiter) {
     limit2d_kernel<TC, TS><<<grid1d(n), 256, 0, c.stream>>>(Vn, Un, c.nx, c.ny, c.dx, c.dy, c.gamma);
     limit2d_kernel<TC, TS><<<grid1d(n), 256, 0, c.stream>>>(V1, U1, c.nx, c.ny, c.dx, c.dy, c.gamma);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -807,7 +930,11 @@ cudaError_t reverse_step(const AdjointCall& c, const Work& w, const double* lam_
                                  mu1)) != cudaSuccess)
     return e;
   // lam1 = J_Lambda(V1)^T mu1
-  if (c.limiter) {
+  if (c.limiter && c.eq) {
+    limit_vjp2d_mhd_kernel<TC, TS><<<grid1d(n), 128, 0, c.stream>>>(V1, mu1, lam1, c.nx, c.ny,
+                                                                    c.dx, c.dy, c.gamma);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if (c.limiter) {
     limit_vjp2d_kernel<TC, TS><<<grid1d(n), 128, 0, c.stream>>>(V1, mu1, lam1, c.nx, c.ny, c.dx,
                                                                 c.dy, c.gamma);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -819,7 +946,11 @@ cudaError_t reverse_step(const AdjointCall& c, const Work& w, const double* lam_
   if ((e = apply_rhs_vjp<TC, TS>(c, w, Un, lam1, lam_next, 0.5, lam1, 1.0, dt, dst)) != cudaSuccess)
     return e;
   // lam^n = J_Lambda(V^n)^T mu0
-  if (c.limiter) {
+  if (c.limiter && c.eq) {
+    limit_vjp2d_mhd_kernel<TC, TS><<<grid1d(n), 128, 0, c.stream>>>(Vn, mu0, lam_prev, c.nx,
+                                                                    c.ny, c.dx, c.dy, c.gamma);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if (c.limiter) {
     limit_vjp2d_kernel<TC, TS><<<grid1d(n), 128, 0, c.stream>>>(Vn, mu0, lam_prev, c.nx, c.ny,
                                                                 c.dx, c.dy, c.gamma);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

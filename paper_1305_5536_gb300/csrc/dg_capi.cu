@@ -985,8 +985,6 @@ dg_status dg_adjoint_step(dg_ctx* c, const double* lam_next, double* lam_prev, c
     return fail(c, DG_EINVAL, "the adjoint covers the min/max limiter (limiter 0 or 1)");
   if (c->dim != 2 || c->probs.size() != 1)
     return fail(c, DG_EINVAL, "the adjoint is implemented for one 2D problem");
-  if (c->eq == DG_MHD && c->limiter != 0)
-    return fail(c, DG_EINVAL, "the planar MHD adjoint is that of the step without a limiter");
   if (!(dt > 0.0)) return fail(c, DG_EINVAL, "dt must be > 0");
   AdjointCall call;
   call.nx = c->probs[0].nx; call.ny = c->probs[0].ny;
@@ -1009,8 +1007,6 @@ dg_status dg_record(dg_ctx* c, int nsteps, double dt_override, double* t_out) {
     return fail(c, DG_EINVAL, "the adjoint covers the min/max limiter (limiter 0 or 1)");
   if (c->dim != 2 || c->probs.size() != 1)
     return fail(c, DG_EINVAL, "the adjoint is implemented for one 2D problem");
-  if (c->eq == DG_MHD && c->limiter != 0)
-    return fail(c, DG_EINVAL, "the planar MHD adjoint is that of the step without a limiter");
   if (nsteps < 0) return fail(c, DG_EINVAL, "nsteps must be >= 0");
   const Prob& p = c->probs[0];
   std::string msg;

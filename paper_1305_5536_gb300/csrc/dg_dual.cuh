@@ -148,6 +148,16 @@ __device__ __forceinline__ bool operator>=(const Dn<T, N>& a, const Dn<T, N>& b)
 template <class T, int N>
 __device__ __forceinline__ Dn<T, N> fabs(const Dn<T, N>& a) { return dabs(a); }
 template <class T, int N>
+__device__ __forceinline__ Dn<T, N>& operator*=(Dn<T, N>& a, const Dn<T, N>& b) {
+  a = a * b;
+  return a;
+}
+template <class T, int N>
+__device__ __forceinline__ Dn<T, N>& operator+=(Dn<T, N>& a, const Dn<T, N>& b) {
+  a = a + b;
+  return a;
+}
+template <class T, int N>
 __device__ __forceinline__ Dn<T, N> rsqrtv(const Dn<T, N>& a) { return dsqrt(a); }
 template <class T, int N>
 struct Prec<Dn<T, N>> {
